@@ -1,0 +1,188 @@
+/*
+ * kpynq.h -- C ABI of the GB300 (sm_103a) work-efficient triangle-inequality
+ * K-means library (libkpynq.so).
+ *
+ * The method is KPynq's (Abstract; Sec. I): K-means whose assignment step runs
+ * a "Multi-level Filter" -- a group-level filter and a point-level filter over
+ * per-point distance bounds -- before a "Distance Calculator" that evaluates
+ * only the point-centroid pairs the filters could not rule out.  The filters
+ * discard only evaluations that cannot change a point's nearest centroid, so
+ * the result is that of standard (Lloyd) K-means.  The paper gives no formulas;
+ * the bound bookkeeping follows the group/point filter scheme of Yinyang
+ * K-means, and every reading is stated where it is used.
+ *
+ * Definitions used by every call:
+ *   assignment  a(x) = argmin_k ||x - c_k||^2, ties to the lowest index k.
+ *               Labels are exact: equal to the FP64 argmin over the library's
+ *               (FP32) centroids, whatever the filters skipped.
+ *   update      c_k <- mean of the points assigned to k (FP64 sums); an empty
+ *               cluster keeps its centroid.
+ *   iteration t assign from C^t, then update to C^{t+1}.  Iteration 0 is a
+ *               dense pass over all K centroids; later ones are filtered.
+ *   objective   J_t = sum_x ||x - c^t_{a_t(x)}||^2 (FP64).
+ *   stop rule   (kmeans_fit) after max_iter iterations, when no label changed,
+ *               or when J_{t-1} - J_t < tol * J_{t-1}.
+ *
+ * Pointers.  Every array argument may be a host or a device pointer; the
+ * library asks the CUDA runtime which (cudaPointerGetAttributes).  Device
+ * pointers must be on the context's device.  Host input arrays are copied to
+ * library-owned device memory; host output arrays are filled by a
+ * device-to-host copy before the call returns.  Layouts are row-major and
+ * dense: X is N x D float32, centroids K x D float32, labels N int32.
+ *
+ * Ownership.  A device X is borrowed, not copied: it must stay valid and
+ * unchanged until kmeans_destroy.  All other state (bounds, sums, queues) is
+ * allocated by kmeans_init and freed by kmeans_destroy.
+ *
+ * Streams.  All work is ordered on the stream given in kmeans_options (NULL =
+ * the legacy default stream).  kmeans_iterate, kmeans_fit and the getters
+ * return after that stream has finished their work.
+ *
+ * Errors.  Every call returns a km_status.  The library never aborts the
+ * process; kmeans_last_error gives a message.  A call that fails with
+ * KM_ECUDA or KM_ETIMEOUT leaves the context unusable (KM_ESTATE afterwards).
+ *
+ * Threads.  A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef KPYNQ_H
+#define KPYNQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KM_API __attribute__((visibility("default")))
+#else
+#define KM_API
+#endif
+
+typedef struct kmeans_ctx kmeans_ctx;
+
+typedef enum {
+    KM_OK = 0,
+    KM_EINVAL = -1,   /* bad argument: sizes, null pointer, non-finite input */
+    KM_ENOMEM = -2,   /* device or host allocation failed */
+    KM_ECUDA = -3,    /* a CUDA runtime call or kernel failed */
+    KM_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    KM_ESTATE = -5    /* context unusable after an earlier failure */
+} km_status;
+
+/* kmeans_options.algo */
+enum {
+    KM_ALGO_FILTERED = 0, /* group + point filters, survivor distances */
+    KM_ALGO_LLOYD = 1     /* plain Lloyd: every distance, every iteration */
+};
+
+/* kmeans_options.grouping: how the K centroids form the G groups */
+enum {
+    KM_GROUP_CONTIGUOUS = 0 /* centroid j -> group floor(j * G / K) */
+};
+
+typedef struct {
+    int32_t algo;        /* KM_ALGO_* */
+    int32_t grouping;    /* KM_GROUP_* */
+    int32_t validate;    /* nonzero: reject X / init_centroids with NaN or Inf */
+    int32_t reserved0;
+    void *stream;        /* cudaStream_t; NULL = legacy default stream */
+    int64_t reserved[6]; /* must be zero */
+} kmeans_options;
+
+/* Per-iteration statistics (all counts are for that iteration). */
+typedef struct {
+    int32_t iter;          /* t */
+    int32_t done;          /* the stop rule held after this iteration */
+    int64_t n_changed;     /* labels that changed (N at t = 0) */
+    int64_t n_survivors;   /* points not kept by the global filter */
+    int64_t n_scanned;     /* points still unresolved after tightening u */
+    int64_t n_dist;        /* point-centroid distances evaluated */
+    int64_t n_recheck;     /* points whose label was settled in FP64 */
+    double objective;      /* J_t = J(a_t, C^t) */
+    double max_drift;      /* max_k ||c_k^{t+1} - c_k^t|| (rounded up) */
+} kmeans_iter_stats;
+
+/* Fill *opt with defaults: filtered algorithm, contiguous groups, no
+ * validation, default stream. */
+KM_API void kmeans_default_options(kmeans_options *opt);
+
+/*
+ * Create a context for one problem and store the initial centroids C^0.
+ * X: N x D float32 (host or device; a device X is borrowed).
+ * init_centroids: K x D float32 (host or device; copied).
+ * Requires 1 <= K <= N < 2^31, 1 <= D <= 4096, 1 <= G <= K, K <= 65535.
+ * opt may be NULL (defaults).  On success *out receives the context.
+ * Errors: KM_EINVAL (bad sizes / null pointers / non-finite data when
+ * validating), KM_ENOMEM, KM_ECUDA.  On failure *out is NULL and
+ * kmeans_last_error(NULL) describes the failure (per thread).
+ */
+KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D,
+                       int32_t K, int32_t G, const float *init_centroids,
+                       const kmeans_options *opt);
+
+/*
+ * Run one iteration t: assignment from C^t (dense at t = 0, filtered after;
+ * every distance for KM_ALGO_LLOYD), then the centroid update to C^{t+1}
+ * with drift.  stats (nullable) receives the iteration's statistics.
+ * Blocks until the iteration has finished on the device.
+ */
+KM_API int kmeans_iterate(kmeans_ctx *ctx, kmeans_iter_stats *stats);
+
+/*
+ * Iterate from the current state until the stop rule holds (at most max_iter
+ * iterations in this call; tol >= 0), then assign every point to the returned
+ * centroids.  Outputs (each nullable; host or device):
+ *   labels    N int32   final assignment to the returned centroids
+ *   centroids K x D f32 the returned centroids
+ *   objective 1 double  J of that pair (FP64)
+ *   n_iter    1 int32   iterations performed by this call
+ * The whole loop is replayed as one CUDA graph with a device-side loop
+ * condition (no host round trip per iteration).
+ */
+KM_API int kmeans_fit(kmeans_ctx *ctx, int32_t max_iter, double tol,
+                      int32_t *labels, float *centroids, double *objective,
+                      int32_t *n_iter);
+
+/* Current labels (the last assignment made) into labels[N]. */
+KM_API int kmeans_get_labels(kmeans_ctx *ctx, int32_t *labels);
+
+/* Current centroids (those the next assignment will use) into C[K x D]. */
+KM_API int kmeans_get_centroids(kmeans_ctx *ctx, float *C);
+
+/* Statistics of iteration t (0 <= t < iterations run so far, at most the
+ * last 4096 iterations are kept). */
+KM_API int kmeans_get_stats(kmeans_ctx *ctx, int32_t t, kmeans_iter_stats *stats);
+
+/*
+ * The per-point bounds, made valid for the current centroids: u[N] (upper
+ * bound on ||x - c_a||), lbg[N] (lower bound on the distance to every other
+ * centroid) and lb[N x G] (lower bound per centroid group, excluding the
+ * point's own centroid).  Each output is nullable.  Only meaningful for
+ * KM_ALGO_FILTERED after at least one iteration.
+ */
+KM_API int kmeans_get_bounds(kmeans_ctx *ctx, float *u, float *lbg, float *lb);
+
+/* Number of iterations run so far on this context. */
+KM_API int kmeans_get_iteration(const kmeans_ctx *ctx, int32_t *t);
+
+/* Free the context and everything it allocated.  NULL is a no-op. */
+KM_API void kmeans_destroy(kmeans_ctx *ctx);
+
+/* Message for the last failure on ctx, or for the calling thread's last
+ * failed kmeans_init when ctx is NULL.  Never NULL. */
+KM_API const char *kmeans_last_error(const kmeans_ctx *ctx);
+
+/* Kernel launches issued from the host by this library in this process (all
+ * contexts; a graph counts its kernels once, when it is recorded). */
+KM_API int64_t kmeans_launch_count(void);
+
+/* Kernels of this context that have run on the device, graph replays
+ * included, as of the end of the last blocking call. */
+KM_API int kmeans_get_kernel_count(const kmeans_ctx *ctx, int64_t *n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KPYNQ_H */

@@ -1,0 +1,543 @@
+// kp_api.cu -- the C ABI declared in include/kpynq.h.
+//
+// Host-side runtime of the library: argument checking, device state
+// allocation, the per-iteration launch sequence, and the fit loop, which is
+// recorded once per context as a CUDA graph whose body (filter -> survivor ->
+// update) runs under a device-side `while` conditional node: the update
+// kernel evaluates the stop rule and sets the loop condition, so a fit costs
+// one graph launch and one final synchronisation.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kp_common.cuh"
+
+namespace kp {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace kp
+
+using namespace kp;
+
+static thread_local char g_init_error[512] = "";
+
+struct kmeans_ctx {
+    int dev = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to record graphs
+    kmeans_options opt{};
+    Params p{};
+    float *X_own = nullptr;
+    int tcap = 0;
+    int t_host = 0;        // iterations run (mirrors ctrl->t after each call)
+    int v_host = 0;        // table version (mirrors ctrl->v)
+    bool broken = false;
+    char err[512] = "";
+    // fit graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    Ctrl *ctrl_host = nullptr;  // pinned mirror of the control block
+    int *flag_dev = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+int set_err(kmeans_ctx *c, int code, const char *fmt, ...) {
+    char *buf = c ? c->err : g_init_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    if (c && (code == KM_ECUDA || code == KM_ETIMEOUT)) c->broken = true;
+    return code;
+}
+
+#define KP_CUDA(c, call)                                                                          \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            int code_ = (e_ == cudaErrorMemoryAllocation) ? KM_ENOMEM : KM_ECUDA;                 \
+            return set_err((c), code_, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                           __FILE__, __LINE__);                                                   \
+        }                                                                                         \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(kmeans_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+int padded_stride_c(int D) {
+    int dp = dense_dp(D);
+    int base = dp > 0 ? dp : ((D + 3) & ~3);
+    // an odd number of 16-byte units per row keeps lane-per-centroid float4
+    // reads of shared memory free of bank conflicts
+    return ((base / 4) % 2 == 0) ? base + 4 : base;
+}
+
+float f32_up(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+float f32_dn(double x) {
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+int sync_and_check(kmeans_ctx *c) {
+    KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    KP_CUDA(c, cudaMemcpy(c->ctrl_host, c->p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    c->t_host = c->ctrl_host->t;
+    c->v_host = c->ctrl_host->v;
+    if (c->ctrl_host->err)
+        return set_err(c, KM_ETIMEOUT, "a bounded device-side wait gave up (code %d)", c->ctrl_host->err);
+    return KM_OK;
+}
+
+// Drift tables must hold `need` more versions: rebase (and grow) if not.
+int ensure_tables(kmeans_ctx *c, int need) {
+    if (c->v_host + need < c->tcap) return KM_OK;
+    Params &p = c->p;
+    if (p.algo == KM_ALGO_FILTERED && c->t_host > 0) {
+        KP_CUDA(c, launch_rebase(p, c->stream, c->num_sms));
+    } else {
+        Params q = p;
+        q.N = 0;
+        KP_CUDA(c, launch_rebase(q, c->stream, c->num_sms));
+    }
+    c->v_host = 0;
+    if (need < c->tcap) return KM_OK;
+    KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    int tcap = ((need + 1 + 63) / 64) * 64;
+    if (tcap > 65536) return set_err(c, KM_EINVAL, "max_iter too large (at most 65534)");
+    float *Dc, *Dg, *Dm;
+    KP_CUDA(c, dalloc(c, &Dc, (size_t)tcap * p.K));
+    KP_CUDA(c, dalloc(c, &Dg, (size_t)tcap * p.Gp));
+    KP_CUDA(c, dalloc(c, &Dm, (size_t)tcap));
+    KP_CUDA(c, cudaMemsetAsync(Dc, 0, (size_t)tcap * p.K * 4, c->stream));
+    KP_CUDA(c, cudaMemsetAsync(Dg, 0, (size_t)tcap * p.Gp * 4, c->stream));
+    KP_CUDA(c, cudaMemsetAsync(Dm, 0, (size_t)tcap * 4, c->stream));
+    p.Dc = Dc;
+    p.Dg = Dg;
+    p.Dm = Dm;
+    c->tcap = tcap;
+    if (c->graph_exec) {  // recorded with the old table pointers
+        cudaGraphExecDestroy(c->graph_exec);
+        cudaGraphDestroy(c->graph);
+        c->graph_exec = nullptr;
+        c->graph = nullptr;
+    }
+    return KM_OK;
+}
+
+// One assignment (dense when `dense`, filtered otherwise), stream-ordered.
+cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool dense, bool first, int respect_done) {
+    cudaError_t e;
+    if (dense) {
+        if ((e = launch_dense_assign(p, s, first, respect_done, c->num_sms)) != cudaSuccess) return e;
+        return launch_apply_moves(p, s, first ? 1 : 0, respect_done, c->num_sms);
+    }
+    if ((e = launch_filter(p, s, respect_done, c->num_sms)) != cudaSuccess) return e;
+    return launch_survivor(p, s, respect_done, c->num_sms, c->smem_optin);
+}
+
+// One full iteration: assignment, then update.
+cudaError_t enqueue_iteration(kmeans_ctx *c, const Params &p, cudaStream_t s, bool first, int respect_done) {
+    const bool dense = first || p.algo == KM_ALGO_LLOYD;
+    cudaError_t e = enqueue_assign(c, p, s, dense, first, respect_done);
+    if (e != cudaSuccess) return e;
+    return launch_update(p, s, 0, respect_done);
+}
+
+// Record the fit graph: set_cond -> while(cond){ iteration } -> final
+// assignment -> objective.
+int build_fit_graph(kmeans_ctx *c) {
+    cudaGraph_t g = nullptr;
+    KP_CUDA(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    KP_CUDA(c, cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    Params p = c->p;
+    p.cond = (unsigned long long)h;
+
+    KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_set_cond(p, c->cap_stream);
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g2);
+    KP_CUDA(c, e);
+    KP_CUDA(c, e2);
+
+    size_t nn = 0;
+    KP_CUDA(c, cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    KP_CUDA(c, cudaGraphGetNodes(g, nodes.data(), &nn));
+    if (nn != 1) return set_err(c, KM_ECUDA, "unexpected graph prologue (%zu nodes)", nn);
+
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond_node;
+    KP_CUDA(c, cudaGraphAddNode(&cond_node, g, nodes.data(), nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    e = enqueue_iteration(c, p, c->cap_stream, false, 1);
+    e2 = cudaStreamEndCapture(c->cap_stream, &body);
+    KP_CUDA(c, e);
+    KP_CUDA(c, e2);
+
+    // epilogue: final assignment to the returned centroids, then J
+    Params pf = c->p;
+    pf.cond = 0;
+    KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, g, &cond_node, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    e = enqueue_assign(c, pf, c->cap_stream, pf.algo == KM_ALGO_LLOYD, false, 0);
+    if (e == cudaSuccess) e = launch_update(pf, c->cap_stream, 1, 0);
+    e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    KP_CUDA(c, e);
+    KP_CUDA(c, e2);
+
+    cudaGraphExec_t ex = nullptr;
+    KP_CUDA(c, cudaGraphInstantiate(&ex, g, 0));
+    c->graph = g;
+    c->graph_exec = ex;
+    c->cond = h;
+    return KM_OK;
+}
+
+int check_ctx(kmeans_ctx *c) {
+    if (!c) return KM_EINVAL;
+    if (c->broken) return set_err(c, KM_ESTATE, "context unusable after an earlier failure");
+    return KM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+KM_API void kmeans_default_options(kmeans_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->algo = KM_ALGO_FILTERED;
+    opt->grouping = KM_GROUP_CONTIGUOUS;
+}
+
+KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, int32_t K, int32_t G,
+                       const float *init_centroids, const kmeans_options *opt) {
+    if (!out) return set_err(nullptr, KM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!X || !init_centroids) return set_err(nullptr, KM_EINVAL, "X or init_centroids is NULL");
+    if (N < 1 || N >= (int64_t)1 << 31) return set_err(nullptr, KM_EINVAL, "N=%lld out of range [1, 2^31)", (long long)N);
+    if (D < 1 || D > 4096) return set_err(nullptr, KM_EINVAL, "D=%d out of range [1, 4096]", D);
+    if (K < 1 || K > 65535 || (int64_t)K > N) return set_err(nullptr, KM_EINVAL, "K=%d must be in [1, min(N, 65535)]", K);
+    if (G < 1 || G > K) return set_err(nullptr, KM_EINVAL, "G=%d must be in [1, K]", G);
+    kmeans_options o;
+    kmeans_default_options(&o);
+    if (opt) o = *opt;
+    if (o.algo != KM_ALGO_FILTERED && o.algo != KM_ALGO_LLOYD) return set_err(nullptr, KM_EINVAL, "unknown algo %d", o.algo);
+    if (o.grouping != KM_GROUP_CONTIGUOUS) return set_err(nullptr, KM_EINVAL, "unknown grouping %d", o.grouping);
+    for (int i = 0; i < 6; ++i)
+        if (o.reserved[i]) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
+
+    kmeans_ctx *c = new (std::nothrow) kmeans_ctx();
+    if (!c) return set_err(nullptr, KM_ENOMEM, "host allocation failed");
+    int rc = KM_OK;
+    auto fail = [&](int code) {
+        snprintf(g_init_error, sizeof(g_init_error), "%s", c->err);
+        kmeans_destroy(c);
+        return code;
+    };
+#define INIT_CUDA(call)                                                                             \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            set_err(c, e_ == cudaErrorMemoryAllocation ? KM_ENOMEM : KM_ECUDA, "%s failed: %s",     \
+                    #call, cudaGetErrorString(e_));                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? KM_ENOMEM : KM_ECUDA);                    \
+        }                                                                                           \
+    } while (0)
+
+    c->opt = o;
+    c->stream = static_cast<cudaStream_t>(o.stream);
+    INIT_CUDA(cudaGetDevice(&c->dev));
+    INIT_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+    int optin = 0;
+    INIT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+    c->smem_optin = (size_t)optin;
+    INIT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    INIT_CUDA(cudaMallocHost(&c->ctrl_host, sizeof(Ctrl)));
+
+    Params &p = c->p;
+    p.N = N;
+    p.D = D;
+    p.K = K;
+    p.G = G;
+    p.Dp = padded_stride_c(D);
+    p.Gp = (G + 3) & ~3;
+    p.algo = o.algo;
+    const bool filtered = o.algo == KM_ALGO_FILTERED;
+
+    // X: borrowed when on the device, copied otherwise
+    if (is_device_ptr(X)) {
+        p.X = X;
+    } else {
+        INIT_CUDA(dalloc(c, &c->X_own, (size_t)N * D));
+        INIT_CUDA(cudaMemcpyAsync(c->X_own, X, (size_t)N * D * 4, cudaMemcpyDefault, c->stream));
+        p.X = c->X_own;
+    }
+    p.x_vec4 = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.X) & 15) == 0);
+
+    INIT_CUDA(dalloc(c, &p.label, (size_t)N));
+    INIT_CUDA(dalloc(c, &p.moved, (size_t)N));
+    INIT_CUDA(dalloc(c, &p.moved_old, (size_t)N));
+    if (filtered) {
+        INIT_CUDA(dalloc(c, &p.u, (size_t)N));
+        INIT_CUDA(dalloc(c, &p.lbg, (size_t)N));
+        INIT_CUDA(dalloc(c, &p.stamp, (size_t)N));
+        INIT_CUDA(dalloc(c, &p.lb, (size_t)N * p.Gp));
+        INIT_CUDA(dalloc(c, &p.queue, (size_t)N));
+    }
+    INIT_CUDA(dalloc(c, &p.C, (size_t)K * p.Dp));
+    INIT_CUDA(dalloc(c, &p.S, (size_t)K * D));
+    INIT_CUDA(dalloc(c, &p.Q, (size_t)K));
+    INIT_CUDA(dalloc(c, &p.cnt, (size_t)K));
+    INIT_CUDA(dalloc(c, &p.delta, (size_t)K));
+    INIT_CUDA(dalloc(c, &p.Jk, (size_t)K));
+    int32_t *grp, *gstart;
+    INIT_CUDA(dalloc(c, &grp, (size_t)K));
+    INIT_CUDA(dalloc(c, &gstart, (size_t)G + 1));
+    p.grp = grp;
+    p.gstart = gstart;
+    INIT_CUDA(dalloc(c, &p.ctrl, 1));
+    INIT_CUDA(dalloc(c, &p.stats, (size_t)kStatsCap));
+    INIT_CUDA(dalloc(c, &c->flag_dev, 1));
+    c->tcap = 64;
+    INIT_CUDA(dalloc(c, &p.Dc, (size_t)c->tcap * K));
+    INIT_CUDA(dalloc(c, &p.Dg, (size_t)c->tcap * p.Gp));
+    INIT_CUDA(dalloc(c, &p.Dm, (size_t)c->tcap));
+    p.tcap = c->tcap;
+
+    cudaStream_t s = c->stream;
+    INIT_CUDA(cudaMemsetAsync(p.C, 0, (size_t)K * p.Dp * 4, s));
+    INIT_CUDA(cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)D * 4, (size_t)D * 4, K,
+                                cudaMemcpyDefault, s));
+    INIT_CUDA(cudaMemsetAsync(p.S, 0, (size_t)K * D * 8, s));
+    INIT_CUDA(cudaMemsetAsync(p.Q, 0, (size_t)K * 8, s));
+    INIT_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)K * 8, s));
+    INIT_CUDA(cudaMemsetAsync(p.Dc, 0, (size_t)c->tcap * K * 4, s));
+    INIT_CUDA(cudaMemsetAsync(p.Dg, 0, (size_t)c->tcap * p.Gp * 4, s));
+    INIT_CUDA(cudaMemsetAsync(p.Dm, 0, (size_t)c->tcap * 4, s));
+    INIT_CUDA(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
+    INIT_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * kStatsCap, s));
+
+    // contiguous grouping: centroid j -> floor(j G / K)
+    std::vector<int32_t> hg(K), hs(G + 1);
+    for (int j = 0; j < K; ++j) hg[j] = (int32_t)(((int64_t)j * G) / K);
+    for (int g = 0; g <= G; ++g) hs[g] = (int32_t)(((int64_t)g * K + G - 1) / G);
+    INIT_CUDA(cudaMemcpyAsync(grp, hg.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
+    INIT_CUDA(cudaMemcpyAsync(gstart, hs.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice, s));
+
+    // FP32 distance error bound: s_fp32 in s [(1-u)^2 (1-g_D), (1+u)^2 (1+g_D)],
+    // u = 2^-24, g_D = D u / (1 - D u) (recursive or tree summation of D
+    // squares, Higham Thm 4.4): eps = (D + 4) u with margin.
+    const double u24 = std::ldexp(1.0, -24);
+    const double eps = (D + 4) * u24 * (1.0 + 1.0 / 1024);
+    p.eps_hi = f32_up(1.0 + 2.0 * eps);
+    p.eps_lo = f32_dn(1.0 - eps);
+    p.tiny = std::ldexp((float)(D + 4), -149);
+
+    if (o.validate) {
+        INIT_CUDA(cudaMemsetAsync(c->flag_dev, 0, 4, s));
+        INIT_CUDA(launch_check_finite(p.X, N * D, c->flag_dev, s, c->num_sms));
+        INIT_CUDA(launch_check_finite(p.C, (int64_t)K * p.Dp, c->flag_dev, s, c->num_sms));
+        int h = 0;
+        INIT_CUDA(cudaMemcpyAsync(&h, c->flag_dev, 4, cudaMemcpyDeviceToHost, s));
+        INIT_CUDA(cudaStreamSynchronize(s));
+        if (h) {
+            set_err(c, KM_EINVAL, "X or init_centroids holds NaN or Inf");
+            return fail(KM_EINVAL);
+        }
+    }
+    INIT_CUDA(cudaStreamSynchronize(s));
+    *out = c;
+    (void)rc;
+    return KM_OK;
+#undef INIT_CUDA
+}
+
+KM_API int kmeans_iterate(kmeans_ctx *c, kmeans_iter_stats *stats) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    DeviceGuard dg(c->dev);
+    if ((rc = ensure_tables(c, 2))) return rc;
+    Params &p = c->p;
+    p.tcap = c->tcap;
+    KP_CUDA(c, launch_arm(p, c->stream, 1, 0.0));
+    KP_CUDA(c, enqueue_iteration(c, p, c->stream, c->t_host == 0, 0));
+    const int t = c->t_host;
+    if ((rc = sync_and_check(c))) return rc;
+    if (stats) KP_CUDA(c, cudaMemcpy(stats, p.stats + (t % kStatsCap), sizeof(*stats), cudaMemcpyDeviceToHost));
+    return KM_OK;
+}
+
+KM_API int kmeans_fit(kmeans_ctx *c, int32_t max_iter, double tol, int32_t *labels, float *centroids,
+                      double *objective, int32_t *n_iter) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (max_iter < 0 || !(tol >= 0.0)) return set_err(c, KM_EINVAL, "max_iter must be >= 0 and tol >= 0");
+    DeviceGuard dg(c->dev);
+    if ((rc = ensure_tables(c, max_iter + 2))) return rc;
+    Params &p = c->p;
+    p.tcap = c->tcap;
+    KP_CUDA(c, launch_arm(p, c->stream, max_iter, tol));
+    if (c->t_host == 0 && max_iter == 0) {
+        // nothing to iterate and no bounds yet: a dense assignment to C^0
+        KP_CUDA(c, enqueue_assign(c, p, c->stream, true, true, 0));
+        KP_CUDA(c, launch_update(p, c->stream, 1, 0));
+    } else {
+        if (!c->graph_exec && (rc = build_fit_graph(c))) return rc;
+        if (c->t_host == 0) KP_CUDA(c, enqueue_iteration(c, p, c->stream, true, 1));
+        KP_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    }
+    if ((rc = sync_and_check(c))) return rc;
+    cudaStream_t s = c->stream;
+    if (labels) KP_CUDA(c, cudaMemcpyAsync(labels, p.label, (size_t)p.N * 4, cudaMemcpyDefault, s));
+    if (centroids)
+        KP_CUDA(c, cudaMemcpy2DAsync(centroids, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K,
+                                     cudaMemcpyDefault, s));
+    if (objective) KP_CUDA(c, cudaMemcpyAsync(objective, &p.ctrl->jfinal, 8, cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaStreamSynchronize(s));
+    if (n_iter) {
+        int32_t ni = c->ctrl_host->fit_n_iter;
+        if (is_device_ptr(n_iter)) KP_CUDA(c, cudaMemcpy(n_iter, &ni, 4, cudaMemcpyHostToDevice));
+        else *n_iter = ni;
+    }
+    return KM_OK;
+}
+
+KM_API int kmeans_get_labels(kmeans_ctx *c, int32_t *labels) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!labels) return set_err(c, KM_EINVAL, "labels is NULL");
+    DeviceGuard dg(c->dev);
+    KP_CUDA(c, cudaMemcpyAsync(labels, c->p.label, (size_t)c->p.N * 4, cudaMemcpyDefault, c->stream));
+    KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KM_OK;
+}
+
+KM_API int kmeans_get_centroids(kmeans_ctx *c, float *C) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!C) return set_err(c, KM_EINVAL, "C is NULL");
+    DeviceGuard dg(c->dev);
+    const Params &p = c->p;
+    KP_CUDA(c, cudaMemcpy2DAsync(C, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K, cudaMemcpyDefault,
+                                 c->stream));
+    KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KM_OK;
+}
+
+KM_API int kmeans_get_stats(kmeans_ctx *c, int32_t t, kmeans_iter_stats *stats) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!stats) return set_err(c, KM_EINVAL, "stats is NULL");
+    if (t < 0 || t >= c->t_host || t < c->t_host - kStatsCap)
+        return set_err(c, KM_EINVAL, "no statistics kept for iteration %d", t);
+    DeviceGuard dg(c->dev);
+    KP_CUDA(c, cudaMemcpyAsync(stats, c->p.stats + (t % kStatsCap), sizeof(*stats), cudaMemcpyDefault, c->stream));
+    KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KM_OK;
+}
+
+KM_API int kmeans_get_bounds(kmeans_ctx *c, float *u, float *lbg, float *lb) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (c->p.algo != KM_ALGO_FILTERED || c->t_host == 0)
+        return set_err(c, KM_EINVAL, "bounds exist only for the filtered algorithm after an iteration");
+    DeviceGuard dg(c->dev);
+    const Params &p = c->p;
+    float *outs[3] = {u, lbg, lb};
+    size_t sizes[3] = {(size_t)p.N, (size_t)p.N, (size_t)p.N * p.G};
+    float *dev[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) {
+        if (!outs[i]) continue;
+        if (is_device_ptr(outs[i])) dev[i] = outs[i];
+        else KP_CUDA(c, cudaMallocAsync(&dev[i], sizes[i] * 4, c->stream));
+    }
+    KP_CUDA(c, launch_bounds_out(p, c->stream, dev[0], dev[1], dev[2], c->num_sms));
+    for (int i = 0; i < 3; ++i) {
+        if (outs[i] && dev[i] != outs[i]) {
+            KP_CUDA(c, cudaMemcpyAsync(outs[i], dev[i], sizes[i] * 4, cudaMemcpyDeviceToHost, c->stream));
+            KP_CUDA(c, cudaFreeAsync(dev[i], c->stream));
+        }
+    }
+    KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KM_OK;
+}
+
+KM_API int kmeans_get_kernel_count(const kmeans_ctx *c, int64_t *n) {
+    if (!c || !n) return KM_EINVAL;
+    *n = (int64_t)c->ctrl_host->kernels;
+    return KM_OK;
+}
+
+KM_API int kmeans_get_iteration(const kmeans_ctx *c, int32_t *t) {
+    if (!c || !t) return KM_EINVAL;
+    *t = c->t_host;
+    return KM_OK;
+}
+
+KM_API void kmeans_destroy(kmeans_ctx *c) {
+    if (!c) return;
+    DeviceGuard dg(c->dev);
+    if (c->stream || c->cap_stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (void *q : c->allocs) cudaFree(q);
+    if (c->ctrl_host) cudaFreeHost(c->ctrl_host);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+KM_API const char *kmeans_last_error(const kmeans_ctx *c) { return c ? c->err : g_init_error; }
+
+KM_API int64_t kmeans_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// kp_common.cuh -- state layout, launch parameters and device helpers shared
+// by the kernels of libkpynq (GB300, sm_103a).
+//
+// Bounds (KPynq Sec. I: the multi-level filters test per-point distance
+// bounds; the bookkeeping follows the Yinyang group/point filter scheme):
+//   u(x)     >= ||x - c_a||                 upper bound, own centroid
+//   lbg(x)   <= ||x - c||, every c != a     global lower bound
+//   lb_g(x)  <= ||x - c||, c in group g, c != a
+// They are stored LAZILY: each point keeps the centroid-table version at which
+// its values were exact, and the drift accumulated since then is applied when
+// the point is read.  Cumulative drift tables (all rounded up):
+//   Dc[v][k] = sum_{s<=v} delta_k(s)      per centroid
+//   Dg[v][g] = sum_{s<=v} max_{k in g} delta_k(s)
+//   Dm[v]    = sum_{s<=v} max_k delta_k(s)
+// so that, for a point stamped at version w and centroids at version v,
+//   u_eff   = u + (Dc[v][a] - Dc[w][a])          (rounded up)
+//   lbg_eff = lbg - (Dm[v] - Dm[w])              (rounded down)
+//   lb_eff  = lb_g - (Dg[v][g] - Dg[w][g])       (rounded down)
+// Rounding every cumulative sum upward makes each difference an upper bound on
+// the true drift over (w, v], so the bounds stay valid in FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kpynq.h"
+
+namespace kp {
+
+constexpr int kWarp = 32;
+constexpr int kStatsCap = 4096;
+
+// Device-side control block (one per context).
+struct Ctrl {
+    int32_t v;            // version of the current centroids C (table row)
+    int32_t t;            // iterations run so far
+    int32_t done;         // stop rule met (fit loop)
+    int32_t err;          // nonzero: a bounded device wait gave up
+    int32_t iters_left;   // iterations left in the current fit call
+    int32_t have_jprev;   // J_{t-1} known
+    int32_t queue_count;  // survivors appended by the filter kernel
+    int32_t moved_count;  // moved points appended by the dense kernel
+    uint32_t ticket;      // last-block-done counter of the update kernel
+    int32_t final_pass;   // the current assignment is a fit's final one
+    double tol;
+    double jprev;
+    double jfinal;
+    unsigned long long n_changed, n_survivors, n_scanned, n_dist, n_recheck;
+    int32_t fit_n_iter;   // iterations performed by the current fit call
+    int32_t pad0;
+    unsigned long long kernels;  // kernels of this context run on the device
+};
+
+// every kernel of a context counts itself once (block 0, thread 0)
+__device__ __forceinline__ void count_kernel(Ctrl *c) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->kernels, 1ull);
+}
+
+// Everything a kernel needs, passed by value.
+struct Params {
+    const float *X;      // N x D, row-major
+    int64_t N;
+    int32_t D, K, G;
+    int32_t Dp;          // centroid row stride (floats), >= D, multiple of 4
+    int32_t Gp;          // lb row stride (floats), >= G, multiple of 4
+    int32_t tcap;        // rows of the drift tables
+    int32_t x_vec4;      // X rows are 16-byte aligned and D % 4 == 0
+
+    int32_t *label;      // N
+    float *u;            // N
+    float *lbg;          // N
+    float *lb;           // N x Gp
+    uint32_t *stamp;     // N: (version of u) << 16 | (version of lbg, lb)
+
+    float *C;            // K x Dp (padding columns are zero)
+    double *S;           // K x D   cluster sums (FP64)
+    double *Q;           // K       sum of ||x||^2 per cluster (FP64)
+    unsigned long long *cnt;  // K  cluster sizes
+
+    float *Dc;           // tcap x K
+    float *Dg;           // tcap x Gp
+    float *Dm;           // tcap
+    const int32_t *grp;  // K: group of each centroid
+    const int32_t *gstart;  // G + 1: centroids of group g are [gstart[g], gstart[g+1])
+
+    int32_t *queue;      // N: survivors of the global filter
+    int32_t *moved;      // N: points whose label changed (dense path)
+    int32_t *moved_old;  // N: their previous label (-1: none)
+    float *delta;        // K: drift of the last update
+    double *Jk;          // K: per-cluster objective terms
+
+    Ctrl *ctrl;
+    kmeans_iter_stats *stats;  // kStatsCap ring
+
+    float eps_hi;        // s_true <= s_fp32 * eps_hi + tiny
+    float eps_lo;        // s_true >= s_fp32 * eps_lo - tiny
+    float tiny;          // absolute slack for underflow
+    int32_t algo;
+    unsigned long long cond;  // cudaGraphConditionalHandle of the fit loop (0: none)
+};
+
+// ---------------------------------------------------------------------------
+// directed-rounding distance bounds from an FP32 squared distance
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dist_up(float s, const Params &p) {
+    return __fsqrt_ru(__fadd_ru(__fmul_ru(s, p.eps_hi), p.tiny));
+}
+__device__ __forceinline__ float dist_dn(float s, const Params &p) {
+    return __fsqrt_rd(fmaxf(__fsub_rd(__fmul_rd(s, p.eps_lo), p.tiny), 0.0f));
+}
+// true squared distances of a (computed sa) and b (computed sb) may be ordered
+// either way: the FP32 results cannot settle the argmin
+__device__ __forceinline__ bool unresolved(float sa, float sb, const Params &p) {
+    return __fsub_rd(__fmul_rd(sb, p.eps_lo), p.tiny) <= __fadd_ru(__fmul_ru(sa, p.eps_hi), p.tiny);
+}
+
+// FP64 squared distance with the summation order of the FP64 definition
+// (i ascending, no fused multiply-add): used to settle near-ties exactly.
+__device__ __forceinline__ double dist2_f64(const float *x, const float *c, int D) {
+    double s = 0.0;
+    for (int i = 0; i < D; ++i) {
+        double t = __dsub_rn((double)x[i], (double)c[i]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// warp reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// (value, index) minimum, ties to the lower index; every lane gets the result
+__device__ __forceinline__ void warp_argmin(float &v, int &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov < v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+}
+__device__ __forceinline__ void warp_argmin_d(double &v, int &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov < v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy global -> shared, completed on an mbarrier (bounded waits)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// one bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `phase` of the barrier, giving up after `limit` polls (each
+// try_wait itself blocks for a bounded time).  Returns false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+constexpr uint32_t kWaitPolls = 1u << 20;
+
+// Stage `bytes` (multiple of 16, in chunks) from global to shared with TMA bulk
+// copies issued by thread 0; all threads of the block wait.  On a time-out the
+// block records KM_ETIMEOUT in ctrl->err, waits (bounded) once more for the
+// copies in flight and returns false.
+__device__ inline bool stage_to_smem(void *dst, const void *src, uint32_t bytes, uint64_t *bar, Ctrl *ctrl) {
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        constexpr uint32_t kChunk = 1u << 16;
+        mbar_arrive_expect_tx(bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += kChunk) {
+            uint32_t n = bytes - off < kChunk ? bytes - off : kChunk;
+            tma_bulk_g2s(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, n, bar);
+        }
+    }
+    __syncthreads();
+    bool ok = mbar_wait_bounded(bar, 0, kWaitPolls);
+    if (!ok) {
+        atomicExch(&ctrl->err, (int)KM_ETIMEOUT);
+        mbar_wait_bounded(bar, 0, kWaitPolls);
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t stamp_u(uint32_t s) { return s >> 16; }
+__device__ __forceinline__ uint32_t stamp_l(uint32_t s) { return s & 0xffffu; }
+__device__ __forceinline__ uint32_t make_stamp(uint32_t vu, uint32_t vl) { return (vu << 16) | vl; }
+
+// drift of centroid k between versions w and v (upper bound)
+__device__ __forceinline__ float drift_c(const Params &p, int v, int w, int k) {
+    return v == w ? 0.0f : __fsub_ru(p.Dc[(size_t)v * p.K + k], p.Dc[(size_t)w * p.K + k]);
+}
+__device__ __forceinline__ float drift_g(const Params &p, int v, int w, int g) {
+    return v == w ? 0.0f : __fsub_ru(p.Dg[(size_t)v * p.Gp + g], p.Dg[(size_t)w * p.Gp + g]);
+}
+__device__ __forceinline__ float drift_m(const Params &p, int v, int w) {
+    return v == w ? 0.0f : __fsub_ru(p.Dm[v], p.Dm[w]);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+void count_launch();
+int dense_dp(int D);  // register tile width used for D (0 = generic path)
+
+cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);
+cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms);
+cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms);
+cudaError_t launch_survivor(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit);
+cudaError_t launch_update(const Params &p, cudaStream_t s, int final_only, int respect_done);
+cudaError_t launch_arm(const Params &p, cudaStream_t s, int max_iter, double tol);
+cudaError_t launch_set_cond(const Params &p, cudaStream_t s);
+cudaError_t launch_rebase(const Params &p, cudaStream_t s, int num_sms);
+cudaError_t launch_bounds_out(const Params &p, cudaStream_t s, float *u, float *lbg, float *lb, int num_sms);
+cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t s, int num_sms);
+
+}  // namespace kp

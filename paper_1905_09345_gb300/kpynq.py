@@ -1,0 +1,257 @@
+"""Thin ctypes binding of ``libkpynq.so`` (declared in ``include/kpynq.h``).
+
+The functions below carry the C names and only marshal arguments: every step
+of the K-means iteration runs in the library's CUDA kernels.  Arrays may be
+PyTorch tensors (host or CUDA), NumPy arrays, or raw integer addresses; the
+library itself tells host from device memory.  If the library has not been
+built, loading fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libkpynq.so")
+
+KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ESTATE = 0, -1, -2, -3, -4, -5
+KM_ALGO_FILTERED, KM_ALGO_LLOYD = 0, 1
+KM_GROUP_CONTIGUOUS = 0
+STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ENOMEM", -3: "KM_ECUDA", -4: "KM_ETIMEOUT",
+                -5: "KM_ESTATE"}
+
+
+class KMeansError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kmeans_options(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("grouping", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("reserved", ctypes.c_int64 * 6)]
+
+
+class kmeans_iter_stats(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int32), ("done", ctypes.c_int32), ("n_changed", ctypes.c_int64),
+                ("n_survivors", ctypes.c_int64), ("n_scanned", ctypes.c_int64), ("n_dist", ctypes.c_int64),
+                ("n_recheck", ctypes.c_int64), ("objective", ctypes.c_double), ("max_drift", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libkpynq.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "or python -m paper_1905_09345_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.kmeans_default_options.argtypes = [ctypes.POINTER(kmeans_options)]
+        L.kmeans_default_options.restype = None
+        L.kmeans_init.argtypes = [ctypes.POINTER(vp), vp, i64, i32, i32, i32, vp, ctypes.POINTER(kmeans_options)]
+        L.kmeans_init.restype = ctypes.c_int
+        L.kmeans_iterate.argtypes = [vp, ctypes.POINTER(kmeans_iter_stats)]
+        L.kmeans_iterate.restype = ctypes.c_int
+        L.kmeans_fit.argtypes = [vp, i32, dbl, vp, vp, vp, vp]
+        L.kmeans_fit.restype = ctypes.c_int
+        L.kmeans_get_labels.argtypes = [vp, vp]
+        L.kmeans_get_labels.restype = ctypes.c_int
+        L.kmeans_get_centroids.argtypes = [vp, vp]
+        L.kmeans_get_centroids.restype = ctypes.c_int
+        L.kmeans_get_stats.argtypes = [vp, i32, ctypes.POINTER(kmeans_iter_stats)]
+        L.kmeans_get_stats.restype = ctypes.c_int
+        L.kmeans_get_bounds.argtypes = [vp, vp, vp, vp]
+        L.kmeans_get_bounds.restype = ctypes.c_int
+        L.kmeans_get_iteration.argtypes = [vp, ctypes.POINTER(i32)]
+        L.kmeans_get_iteration.restype = ctypes.c_int
+        L.kmeans_get_kernel_count.argtypes = [vp, ctypes.POINTER(i64)]
+        L.kmeans_get_kernel_count.restype = ctypes.c_int
+        L.kmeans_destroy.argtypes = [vp]
+        L.kmeans_destroy.restype = None
+        L.kmeans_last_error.argtypes = [vp]
+        L.kmeans_last_error.restype = ctypes.c_char_p
+        L.kmeans_launch_count.argtypes = []
+        L.kmeans_launch_count.restype = i64
+        _lib = L
+    return _lib
+
+
+def _addr(a) -> int | None:
+    """Address of a tensor / array / integer (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):  # torch.Tensor
+        if not a.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):  # numpy
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _check(rc: int, ctx=None):
+    if rc != KM_OK:
+        msg = lib().kmeans_last_error(ctx).decode(errors="replace")
+        raise KMeansError(rc, msg)
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def kmeans_default_options() -> kmeans_options:
+    o = kmeans_options()
+    lib().kmeans_default_options(ctypes.byref(o))
+    return o
+
+
+def kmeans_init(X, N: int, D: int, K: int, G: int, init_centroids, opt: kmeans_options | None = None):
+    """Returns the opaque context handle (an int)."""
+    ctx = ctypes.c_void_p()
+    rc = lib().kmeans_init(ctypes.byref(ctx), _addr(X), N, D, K, G, _addr(init_centroids),
+                           ctypes.byref(opt) if opt is not None else None)
+    _check(rc, None)
+    return ctx.value
+
+
+def kmeans_iterate(ctx) -> dict:
+    st = kmeans_iter_stats()
+    _check(lib().kmeans_iterate(ctx, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def kmeans_fit(ctx, max_iter: int, tol: float, labels=None, centroids=None, objective=None, n_iter=None):
+    """Outputs go to the given arrays (host or device); when ``objective`` /
+    ``n_iter`` are None, their values are returned as ``(n_iter, objective)``."""
+    J = ctypes.c_double()
+    ni = ctypes.c_int32()
+    rc = lib().kmeans_fit(ctx, max_iter, tol, _addr(labels), _addr(centroids),
+                          _addr(objective) if objective is not None else ctypes.addressof(J),
+                          _addr(n_iter) if n_iter is not None else ctypes.addressof(ni))
+    _check(rc, ctx)
+    return ni.value, J.value
+
+
+def kmeans_get_labels(ctx, labels) -> None:
+    _check(lib().kmeans_get_labels(ctx, _addr(labels)), ctx)
+
+
+def kmeans_get_centroids(ctx, C) -> None:
+    _check(lib().kmeans_get_centroids(ctx, _addr(C)), ctx)
+
+
+def kmeans_get_stats(ctx, t: int) -> dict:
+    st = kmeans_iter_stats()
+    _check(lib().kmeans_get_stats(ctx, t, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def kmeans_get_bounds(ctx, u=None, lbg=None, lb=None) -> None:
+    _check(lib().kmeans_get_bounds(ctx, _addr(u), _addr(lbg), _addr(lb)), ctx)
+
+
+def kmeans_get_iteration(ctx) -> int:
+    t = ctypes.c_int32()
+    _check(lib().kmeans_get_iteration(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def kmeans_get_kernel_count(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(lib().kmeans_get_kernel_count(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def kmeans_destroy(ctx) -> None:
+    if ctx:
+        lib().kmeans_destroy(ctx)
+
+
+def kmeans_last_error(ctx=None) -> str:
+    return lib().kmeans_last_error(ctx).decode(errors="replace")
+
+
+def kmeans_launch_count() -> int:
+    return lib().kmeans_launch_count()
+
+
+# ---------------------------------------------------------------------------
+# convenience: a context that owns its handle and keeps its inputs alive
+# ---------------------------------------------------------------------------
+@dataclass
+class FitResult:
+    labels: object
+    centroids: object
+    objective: float
+    n_iter: int
+    stats: list
+
+
+class KMeans:
+    """One problem on the GPU.  ``X`` / ``C0``: torch tensors (CUDA or CPU) or
+    NumPy arrays, float32, row-major.  A CUDA ``X`` is borrowed (kept alive by
+    this object)."""
+
+    def __init__(self, X, C0, G: int, *, algo: int = KM_ALGO_FILTERED, stream=None, validate: bool = False):
+        N, D = X.shape
+        K = C0.shape[0]
+        opt = kmeans_default_options()
+        opt.algo = algo
+        opt.validate = int(validate)
+        if stream is not None:
+            opt.stream = stream if isinstance(stream, int) else stream.cuda_stream
+        self._keep = (X, C0)
+        self.N, self.D, self.K, self.G = N, D, K, G
+        self.ctx = kmeans_init(X, N, D, K, G, C0, opt)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            kmeans_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self) -> dict:
+        return kmeans_iterate(self.ctx)
+
+    def fit(self, max_iter: int, tol: float = 0.0, labels=None, centroids=None) -> FitResult:
+        t0 = kmeans_get_iteration(self.ctx)
+        n_iter, J = kmeans_fit(self.ctx, max_iter, tol, labels, centroids)
+        stats = [kmeans_get_stats(self.ctx, t) for t in range(t0, t0 + n_iter)]
+        return FitResult(labels, centroids, J, n_iter, stats)
+
+    def labels(self, out):
+        kmeans_get_labels(self.ctx, out)
+        return out
+
+    def centroids(self, out):
+        kmeans_get_centroids(self.ctx, out)
+        return out
+
+    def bounds(self, u=None, lbg=None, lb=None):
+        kmeans_get_bounds(self.ctx, u, lbg, lb)
+        return u, lbg, lb
+
+    @property
+    def iteration(self) -> int:
+        return kmeans_get_iteration(self.ctx)
+
+    @property
+    def kernel_count(self) -> int:
+        return kmeans_get_kernel_count(self.ctx)

@@ -1,0 +1,95 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol ``include/*.h`` declares, and rejects bad arguments before touching the
+device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1905_09345_gb300 import build, kpynq
+    build.build()
+    return kpynq
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"KM_API\s+[\w\s\*]+?\b(\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ["kmeans_init", "kmeans_iterate", "kmeans_fit", "kmeans_get_labels", "kmeans_get_centroids",
+              "kmeans_destroy", "kmeans_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = L.lib()
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_binding_uses_c_names(L):
+    for n in declared_symbols():
+        assert hasattr(L, n), f"binding lacks {n}"
+
+
+BAD = [
+    dict(N=0, D=4, K=1, G=1),
+    dict(N=10, D=0, K=1, G=1),
+    dict(N=10, D=4097, K=1, G=1),
+    dict(N=10, D=4, K=0, G=1),
+    dict(N=10, D=4, K=11, G=1),
+    dict(N=10, D=4, K=4, G=0),
+    dict(N=10, D=4, K=4, G=5),
+    dict(N=1 << 31, D=4, K=4, G=1),
+    dict(N=100000, D=4, K=65536, G=1),
+]
+
+
+@pytest.mark.parametrize("a", BAD, ids=lambda a: ",".join(f"{k}={v}" for k, v in a.items()))
+def test_init_rejects_bad_sizes(L, a):
+    with pytest.raises(L.KMeansError) as e:
+        L.kmeans_init(16, a["N"], a["D"], a["K"], a["G"], 16)
+    assert e.value.status == L.KM_EINVAL
+    assert L.kmeans_last_error(None)
+
+
+def test_init_rejects_null_and_bad_options(L):
+    with pytest.raises(L.KMeansError) as e:
+        L.kmeans_init(0, 10, 4, 2, 1, 16)
+    assert e.value.status == L.KM_EINVAL
+    opt = L.kmeans_default_options()
+    opt.algo = 7
+    with pytest.raises(L.KMeansError) as e:
+        L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
+    assert e.value.status == L.KM_EINVAL
+    opt = L.kmeans_default_options()
+    opt.reserved[2] = 1
+    with pytest.raises(L.KMeansError) as e:
+        L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
+    assert e.value.status == L.KM_EINVAL
+
+
+def test_null_context_calls(L):
+    lib = L.lib()
+    assert lib.kmeans_iterate(None, None) == L.KM_EINVAL
+    assert lib.kmeans_fit(None, 1, 0.0, None, None, None, None) == L.KM_EINVAL
+    lib.kmeans_destroy(None)
+    assert L.kmeans_launch_count() >= 0
+
+
+def test_default_options(L):
+    o = L.kmeans_default_options()
+    assert o.algo == L.KM_ALGO_FILTERED and o.grouping == L.KM_GROUP_CONTIGUOUS and not o.stream

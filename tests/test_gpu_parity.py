@@ -1,0 +1,329 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Lockstep: before each iteration the GPU's centroids C^t are downloaded; the
+oracle assigns every point to them in FP64 and must give exactly the GPU's
+labels (the library settles every point the FP32 error bound cannot decide in
+FP64, with the oracle's summation order, so no near-tie exception is needed;
+near-ties are still counted).  The GPU's update C^{t+1} must match the
+oracle's update of those labels within 1e-5 relative, and the GPU objective
+J_t the oracle's J(a_t, C^t) within 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_09345_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CENTROID_RTOL = 1e-5
+OBJECTIVE_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def kp():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1905_09345_gb300 import build, kpynq
+    build.build()
+    oracle.build()
+    return kpynq
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_err(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(1.0, np.abs(b).max()))
+
+
+def get_C(km):
+    out = torch.empty(km.K, km.D, dtype=torch.float32, device="cuda")
+    return km.centroids(out).cpu().numpy().astype(np.float64)
+
+
+def get_labels(km):
+    out = torch.empty(km.N, dtype=torch.int32, device="cuda")
+    return km.labels(out).cpu().numpy()
+
+
+def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None):
+    """Run `iters` iterations in lockstep with the oracle; returns the list of
+    per-iteration GPU stats."""
+    N, D = X.shape
+    K = C0.shape[0]
+    km = kp.KMeans(dev(X), dev(C0), G, algo=algo)
+    X64 = X.astype(np.float64)
+    prev = None
+    stats = []
+    near = 0
+    grp = oracle.contiguous_groups(K, G)
+    for t in range(iters):
+        Ct = get_C(km)
+        st = km.iterate()
+        lab = get_labels(km)
+        ref, d1, d2, ch = oracle.lloyd_assign(X64, Ct, prev)
+        near += int(oracle.near_ties(d1, d2).sum()) if K > 1 else 0
+        bad = np.flatnonzero(lab != ref)
+        assert bad.size == 0, f"t={t}: {bad.size} labels differ, first {bad[:5]} gpu {lab[bad[:5]]} ref {ref[bad[:5]]}"
+        assert st["n_changed"] == ch, (t, st["n_changed"], ch)
+        assert st["iter"] == t
+        Cn_ref, counts, J = oracle.lloyd_update(X64, ref, Ct)
+        Cn = get_C(km)
+        assert rel_err(Cn, Cn_ref) <= CENTROID_RTOL, (t, rel_err(Cn, Cn_ref))
+        # FP32 centroids are the FP64 means rounded: within 2 ulp (plus the
+        # FP64 summation-order difference for coordinates that cancel to ~0)
+        tol = 2 * np.spacing(np.abs(Cn_ref).astype(np.float32)) + 1e-10 * (1 + np.abs(Cn_ref).max())
+        assert np.all(np.abs(Cn - Cn_ref) <= tol), t
+        assert abs(st["objective"] - J) <= OBJECTIVE_RTOL * J + 1e-12, (t, st["objective"], J)
+        assert 0 <= st["n_dist"] <= N * K
+        if check_bounds and algo == 0:
+            u = np.empty(N, np.float32)
+            lbg = np.empty(N, np.float32)
+            lb = np.empty((N, G), np.float32)
+            km.bounds(u, lbg, lb)
+            dd = np.sqrt(np.maximum(((X64[:, None, :] - Cn[None, :, :]) ** 2).sum(-1), 0))
+            da = dd[np.arange(N), lab]
+            assert np.all(u >= da * (1 - 1e-12)), f"t={t}: upper bound below distance"
+            dd[np.arange(N), lab] = np.inf
+            assert np.all(lbg <= dd.min(1) * (1 + 1e-12)), f"t={t}: global lower bound above distance"
+            for g in range(G):
+                m = np.where((grp == g)[None, :], dd, np.inf).min(1)
+                assert np.all(lb[:, g] <= m * (1 + 1e-12)), f"t={t}: group {g} lower bound above distance"
+        stats.append(st)
+        prev = ref
+    if report is not None:
+        report["near_ties"] = near
+    km.close()
+    return stats
+
+
+def test_small_blobs_lockstep(kp):
+    """Plain filtered K-means, FP32: N=16,384, D=16, K=16, G=2, 20 iterations."""
+    w = synth.small_blobs()
+    rep = {}
+    st = lockstep(kp, w.X, w.C0, w.G, w.max_iter, report=rep)
+    assert st[0]["n_dist"] == w.N * w.K
+    # the filters remove work once the centroids settle
+    assert sum(s["n_dist"] for s in st[5:]) < 0.5 * w.N * w.K * len(st[5:])
+
+
+def test_small_blobs_fit_matches_oracle_run(kp):
+    w = synth.small_blobs()
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    lab = torch.empty(w.N, dtype=torch.int32, device="cuda")
+    C = torch.empty(w.K, w.D, device="cuda")
+    r = km.fit(w.max_iter, 0.0, lab, C)
+    o = oracle.lloyd_fit(w.X, w.C0, w.max_iter, 0.0)
+    assert r.n_iter == o["n_iter"]
+    lab = lab.cpu().numpy()
+    Cg = C.cpu().numpy().astype(np.float64)
+    assert rel_err(Cg, o["centroids"]) <= CENTROID_RTOL
+    # against the independent FP64 trajectory only near-ties may differ
+    _, d1, d2, _ = oracle.lloyd_assign(w.X, o["centroids"])
+    diff = o["labels"] != lab
+    assert not np.any(diff & ~oracle.near_ties(d1, d2))
+    assert abs(r.objective - o["objective"]) <= 1e-5 * o["objective"]
+    # final labels / objective: exact against the returned centroids
+    ref, _, _, _ = oracle.lloyd_assign(w.X, Cg)
+    assert np.array_equal(lab, ref)
+    assert abs(r.objective - oracle.lloyd_objective(w.X, lab, Cg)) <= OBJECTIVE_RTOL * r.objective
+    for t, s in enumerate(r.stats):
+        assert abs(s["objective"] - o["J_hist"][t]) <= 1e-5 * o["J_hist"][t]
+    km.close()
+
+
+EDGE = [
+    # (N, D, K, G, iters) -- ragged sizes, every register width, generic D
+    (1000, 3, 7, 2, 8),
+    (1001, 17, 33, 5, 8),
+    (2048, 64, 64, 64, 6),
+    (2048, 64, 64, 1, 6),
+    (777, 130, 20, 4, 6),
+    (300, 8, 1, 1, 3),
+    (2000, 1, 5, 2, 8),
+    (3001, 128, 100, 10, 5),
+    (4099, 32, 40, 40, 6),
+    (513, 4, 9, 3, 10),
+]
+
+
+@pytest.mark.parametrize("N,D,K,G,iters", EDGE, ids=[f"N{e[0]}_D{e[1]}_K{e[2]}_G{e[3]}" for e in EDGE])
+def test_edge_shapes_lockstep(kp, N, D, K, G, iters):
+    rng = np.random.default_rng(N * 7 + D)
+    X, _ = synth.gaussian_mixture(rng, N, D, max(K, 2), centre_range=4.0, scale="fixed", scale_args=(1.0,))
+    C0 = synth.sample_init(rng, X, K)
+    lockstep(kp, X, C0, G, iters, check_bounds=(N * K <= 200000))
+
+
+@pytest.mark.parametrize("N,D,K,G,iters", EDGE[:6], ids=[f"N{e[0]}_D{e[1]}_K{e[2]}_G{e[3]}" for e in EDGE[:6]])
+def test_plain_lloyd_lockstep(kp, N, D, K, G, iters):
+    rng = np.random.default_rng(N * 11 + D)
+    X, _ = synth.gaussian_mixture(rng, N, D, max(K, 2), centre_range=4.0, scale="fixed", scale_args=(1.0,))
+    C0 = synth.sample_init(rng, X, K)
+    st = lockstep(kp, X, C0, G, iters, algo=kp.KM_ALGO_LLOYD)
+    assert all(s["n_dist"] == N * K for s in st)
+
+
+def test_bounds_stay_valid(kp):
+    w = synth.small_blobs(N=3000, D=16, K=24, G=5, seed=4)
+    lockstep(kp, w.X, w.C0, w.G, 12, check_bounds=True)
+
+
+def test_exact_ties_go_to_lowest_index(kp):
+    """Integer points and centroids placed symmetrically: many exact ties,
+    including duplicated centroids; the lowest index must win everywhere."""
+    g = np.arange(-6, 7, dtype=np.float32)
+    X = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+    X = np.concatenate([X, np.zeros((X.shape[0], 2), np.float32)], 1)  # D = 4
+    C0 = np.array([[-1, 0, 0, 0], [1, 0, 0, 0], [0, -1, 0, 0], [0, 1, 0, 0], [-1, 0, 0, 0], [3, 3, 0, 0]],
+                  np.float32)
+    st = lockstep(kp, X, C0, 2, 6)
+    assert st[0]["n_recheck"] > 0  # the ties went through the FP64 settle
+
+
+def test_k_equals_n(kp):
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((64, 5)).astype(np.float32)
+    km = kp.KMeans(dev(X), dev(X), 8)
+    lab = torch.empty(64, dtype=torch.int32, device="cuda")
+    r = km.fit(5, 0.0, lab)
+    assert np.array_equal(lab.cpu().numpy(), np.arange(64))
+    assert abs(r.objective) <= 1e-9 and r.n_iter == 2
+    km.close()
+
+
+def test_host_pointers_match_device_pointers(kp):
+    w = synth.small_blobs(N=5000, D=16, K=16, G=4, seed=2)
+    a = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    la = torch.empty(w.N, dtype=torch.int32, device="cuda")
+    Ca = torch.empty(w.K, w.D, device="cuda")
+    ra = a.fit(30, 1e-4, la, Ca)
+    b = kp.KMeans(w.X, w.C0, w.G)  # NumPy (host) inputs
+    lb_ = np.empty(w.N, np.int32)
+    Cb = np.empty((w.K, w.D), np.float32)
+    rb = b.fit(30, 1e-4, lb_, Cb)
+    assert ra.n_iter == rb.n_iter
+    assert np.array_equal(la.cpu().numpy(), lb_)
+    assert np.allclose(Ca.cpu().numpy(), Cb, rtol=1e-6, atol=1e-6)
+    assert abs(ra.objective - rb.objective) <= 1e-9 * ra.objective
+    a.close()
+    b.close()
+
+
+def test_tol_stop_and_continue(kp):
+    """fit() honours tol like the oracle, and a later fit() continues."""
+    w = synth.small_blobs(N=8000, D=16, K=16, G=4, seed=5)
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    o = oracle.lloyd_fit(w.X, w.C0, 50, 1e-3)
+    r = km.fit(50, 1e-3)
+    assert r.n_iter == o["n_iter"]
+    assert abs(r.objective - o["objective"]) <= 1e-5 * o["objective"]
+    t0 = km.iteration
+    r2 = km.fit(3, 0.0)
+    assert km.iteration == t0 + r2.n_iter
+    km.close()
+
+
+def test_iterate_then_fit_and_max_iter_zero(kp):
+    w = synth.small_blobs(N=4000, D=16, K=12, G=3, seed=6)
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    lab = torch.empty(w.N, dtype=torch.int32, device="cuda")
+    r0 = km.fit(0, 0.0, lab)  # assignment to C0 only
+    ref, _, _, _ = oracle.lloyd_assign(w.X, w.C0)
+    assert r0.n_iter == 0 and np.array_equal(lab.cpu().numpy(), ref)
+    km.close()
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    km.iterate()
+    km.iterate()
+    r = km.fit(40, 0.0, lab)
+    o = oracle.lloyd_fit(w.X, w.C0, 42, 0.0)
+    assert 2 + r.n_iter == o["n_iter"]
+    assert np.array_equal(lab.cpu().numpy(), o["labels"])
+    km.close()
+
+
+def test_validate_rejects_nan(kp):
+    X = np.ones((100, 4), np.float32)
+    X[17, 2] = np.nan
+    with pytest.raises(kp.KMeansError) as e:
+        kp.KMeans(dev(X), dev(X[:4] * 0 + 1), 1, validate=True)
+    assert e.value.status == kp.KM_EINVAL
+
+
+def test_long_runs_rebase_and_grow_tables(kp):
+    """More iterations than the drift tables hold at first (64 versions):
+    the library rebases the lazy bounds (and grows the tables for a long
+    fit) and the labels stay exact and the bounds valid."""
+    w = synth.small_blobs(N=3000, D=8, K=40, G=6, seed=8)
+    X64 = w.X.astype(np.float64)
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    for _ in range(70):
+        Ct = get_C(km)
+        km.iterate()
+        ref, _, _, _ = oracle.lloyd_assign(X64, Ct)
+        assert np.array_equal(get_labels(km), ref)
+    assert km.iteration == 70
+    r = km.fit(200, 0.0)  # needs more table rows than allocated: grows
+    C = get_C(km)
+    ref, _, _, _ = oracle.lloyd_assign(X64, C)
+    assert np.array_equal(get_labels(km), ref)
+    u = np.empty(w.N, np.float32)
+    lbg = np.empty(w.N, np.float32)
+    km.bounds(u, lbg)
+    dd = np.sqrt(((X64[:, None, :] - C[None]) ** 2).sum(-1))
+    lab = get_labels(km)
+    assert np.all(u >= dd[np.arange(w.N), lab] * (1 - 1e-12))
+    dd[np.arange(w.N), lab] = np.inf
+    assert np.all(lbg <= dd.min(1) * (1 + 1e-12))
+    assert r.n_iter >= 1
+    km.close()
+
+
+# ---------------------------------------------------------------------------
+# the large workload: N=1,048,576, D=64, K=256, G=26
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def aniso():
+    return synth.anisotropic_1m()
+
+
+def test_aniso_reduced_lockstep(kp):
+    """Same recipe at N=65,536: every iteration checked, with bounds."""
+    w = synth.anisotropic_1m(N=1 << 16)
+    st = lockstep(kp, w.X, w.C0, w.G, 8)
+    assert st[-1]["n_dist"] < 0.5 * w.N * w.K
+
+
+def test_aniso_full_size(kp, aniso):
+    """Full size, in the launch configuration the benchmark times: three
+    lockstep iterations over all points, then the fit to convergence with
+    sampled label checks and exact objective / centroid checks."""
+    w = aniso
+    X64 = w.X.astype(np.float64)
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    prev = None
+    for t in range(2):
+        Ct = get_C(km)
+        st = km.iterate()
+        lab = get_labels(km)
+        ref, d1, d2, ch = oracle.lloyd_assign(X64, Ct, prev)
+        assert np.array_equal(lab, ref), t
+        assert st["n_changed"] == ch
+        Cn_ref, _, J = oracle.lloyd_update(X64, ref, Ct)
+        assert rel_err(get_C(km), Cn_ref) <= CENTROID_RTOL
+        assert abs(st["objective"] - J) <= OBJECTIVE_RTOL * J
+        prev = ref
+    labt = torch.empty(w.N, dtype=torch.int32, device="cuda")
+    Ct = torch.empty(w.K, w.D, device="cuda")
+    r = km.fit(w.max_iter - 2, w.tol, labt, Ct)
+    lab = labt.cpu().numpy()
+    C = Ct.cpu().numpy().astype(np.float64)
+    idx = np.random.default_rng(0).choice(w.N, 1 << 15, replace=False)
+    ref, _, _, _ = oracle.lloyd_assign(X64[idx], C)
+    assert np.array_equal(lab[idx], ref)
+    J = oracle.lloyd_objective(X64, lab, C)
+    assert abs(r.objective - J) <= OBJECTIVE_RTOL * J
+    assert r.stats[-1]["n_dist"] < 0.1 * w.N * w.K
+    km.close()
