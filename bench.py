@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Benchmark: work-efficient triangle-inequality K-means (KPynq) on GB300.
+
+One step = one whole K-means job on the large anisotropic workload
+(N=1,048,576 points, D=64, K=256 centroids, G=26 groups, at most 50 iterations
+or tol 1e-4): restart from C0 (kmeans_reset), then kmeans_fit -- the dense
+iteration 0, the filtered iterations, and the final assignment -- through the
+C ABI, with X resident in HBM.  Metric: points x iterations per second.
+
+The JSON line also carries: plain GPU Lloyd on the same GPU and inputs, the
+fraction of distance evaluations the filters skipped, the roofline of the
+dominant kernel (from a profiled pass that brackets every launch with CUDA
+events on the library's stream), the FP64 oracle timed on the host cores, an
+end-to-end number through the C ABI with host buffers, and SM clocks sampled
+during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (brute-force Lloyd) instead.
+Multi-GPU (torchrun): every rank runs its own replica problem (weak scaling,
+no collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "points*iters/s (filtered K-means, exact labels)"
+UNIT = "points*iters/s"
+L2_BYTES = 129 * 1024 * 1024
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+# the distance loop issues one FSUB and one FFMA per (point, centroid, dim):
+# 3 flops in 2 issue slots of a FP32 lane
+ALU_PEAK_TFLOPS = SMS * FP32_LANES * SM_MAX_GHZ * 1.5 / 1e3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lloyd-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=1 << 20, help="points (default: the full workload)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (timing only; the data path has no collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_ms: float, local_units: float, world_size: int, backend_device=None):
+    """Max step time over ranks and the units all ranks processed.  Uses
+    torch.distributed when world_size > 1 (any backend)."""
+    if world_size == 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=backend_device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world_size: int):
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd[1:1] = ["-i", self.gpu_id]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_uuid():
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else f"GPU-{s}"
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def cpu_baseline(w, n_sample: int, iters: int) -> dict:
+    import oracle
+    oracle.build()
+    Xs = w.X[:n_sample].astype("float64")
+    dt = oracle_iterations(Xs, w.C0.astype("float64"), iters)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n_sample * iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"brute-force FP64 Lloyd (oracle O1: assign + update), first {n_sample} of {w.N} "
+                      f"points, {iters} iterations, K={w.K}, D={w.D}; {dt:.2f} s wall"}
+
+
+def oracle_iterations(Xs, C, iters: int) -> float:
+    """Wall time of `iters` oracle Lloyd iterations (assign + update)."""
+    import oracle
+    t0 = time.perf_counter()
+    prev = None
+    for _ in range(iters):
+        lab, _, _, _ = oracle.lloyd_assign(Xs, C, prev)
+        C, _, _ = oracle.lloyd_update(Xs, lab, C)
+        prev = lab
+    return time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic bytes / flops per launch of each kernel
+# ---------------------------------------------------------------------------
+def algorithmic(kind: str, w, stats: list, launches: int) -> tuple[str, float, str]:
+    """(bound, units per launch, unit) from the per-iteration counters."""
+    N, D, K, G = w.N, w.D, w.K, w.G
+    Gp = (G + 3) // 4 * 4
+    filt = [s for s in stats if s["iter"] > 0]
+    if kind == "dense_assign":
+        return "alu", 3.0 * N * K * D, "flop"
+    if kind == "filter":
+        surv = sum(s["n_survivors"] for s in filt) / max(1, len(filt))
+        return "hbm", 16.0 * N + 4.0 * surv, "byte"
+    if kind == "survivor":
+        surv = sum(s["n_survivors"] for s in filt) / max(1, len(filt))
+        scan = sum(s["n_scanned"] for s in filt) / max(1, len(filt))
+        # per survivor: queue entry, label/stamp/lbg, x row, u/stamp writes;
+        # per scanned point: lb row read + write, label/lbg/u/stamp writes
+        b = surv * (4 + 12 + 4 * D + 8) + scan * (8 * Gp + 16)
+        return "hbm", b, "byte"
+    if kind == "apply_moves":
+        return "hbm", 4.0 * N * D + 4.0 * N, "byte"
+    return "hbm", 0.0, "byte"
+
+
+def source_sha(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "dense_assign": ["paper_1905_09345_gb300/csrc/kp_dense.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "apply_moves": ["paper_1905_09345_gb300/csrc/kp_dense.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "filter": ["paper_1905_09345_gb300/csrc/kp_filter.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "survivor": ["paper_1905_09345_gb300/csrc/kp_filter.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "update": ["paper_1905_09345_gb300/csrc/kp_update.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+}
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_sha") != source_sha(KERNEL_SOURCES.get(kernel, [])):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1905_09345_gb300 import synth
+    w = synth.anisotropic_1m(N=args.n)
+    n_sample = min(w.N, 1 << 16)
+    import oracle
+    oracle.build()
+    Xs = w.X[:n_sample].astype("float64")
+    C0 = w.C0.astype("float64")
+    for _ in range(args.warmup):
+        oracle_iterations(Xs, C0, 1)
+    times = [oracle_iterations(Xs, C0, 1) for _ in range(args.steps)]
+    ms = 1e3 * statistics.mean(times)
+    value = n_sample / (ms / 1e3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "D": w.D, "K": w.K, "G": w.G},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"brute-force FP64 Lloyd (oracle O1): one iteration over the first "
+                                       f"{n_sample} of {w.N} points per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1905_09345_gb300 import kpynq, synth
+    kpynq.lib()
+    w = synth.anisotropic_1m(N=args.n, seed=2 + rank)  # one replica problem per rank
+    dev = torch.device("cuda", local)
+    X = torch.from_numpy(w.X).to(dev)
+    C0 = torch.from_numpy(w.C0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    lab = torch.empty(w.N, dtype=torch.int32, device=dev)
+    C = torch.empty(w.K, w.D, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    log = lambda *a: print(*a, file=sys.stderr, flush=True) if rank == 0 else None
+
+    def timed_steps(km, steps, warmup, label):
+        iters, times, kern, stats = [], [], 0, None
+        for i in range(warmup + steps):
+            flush.zero_()  # L2 flush between steps (outside the timed interval)
+            k0 = km.kernel_count
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            km.reset(C0)
+            r = km.fit(w.max_iter, w.tol, lab, C, with_stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                times.append(e0.elapsed_time(e1))
+                iters.append(r.n_iter)
+                kern += km.kernel_count - k0
+        stats = km.stats(0, iters[-1])
+        log(f"[{label}] {steps} steps: {statistics.mean(times):.3f} ms/step, iters {iters[0]}")
+        return times, iters, kern, stats
+
+    # --- the filtered method (the measured line) ---
+    km = kpynq.KMeans(X, C0, w.G, stream=stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    with ClockSampler(gpu_uuid()) as clk:
+        torch.cuda.synchronize()
+        barrier(ws)
+        times, iters, kern, stats = timed_steps(km, args.steps, args.warmup, "filtered")
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms = statistics.mean(times)
+    units = w.N * statistics.mean(iters)
+    ms_max, units_all = aggregate(ms, units, ws, dev)
+    value = units_all / (ms_max / 1e3)
+    n_dist = sum(s["n_dist"] for s in stats)
+    skip = 1.0 - n_dist / (w.N * w.K * len(stats))
+
+    # --- plain GPU Lloyd on the same GPU and inputs ---
+    lloyd = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream)
+    lt, li, _, _ = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd")
+    lloyd_value = w.N * statistics.mean(li) / (statistics.mean(lt) / 1e3)
+    lloyd.close()
+
+    # --- profiled pass: CUDA events around every launch ---
+    prof = kpynq.KMeans(X, C0, w.G, stream=stream, profile=True)
+    pstats = None
+    kinds = {}
+    for _ in range(args.profile_steps):
+        flush.zero_()
+        prof.reset(C0)
+        r = prof.fit(w.max_iter, w.tol, lab, C)
+        pstats = r.stats
+        for k, (n, t) in prof.profile().items():
+            a = kinds.setdefault(k, [0, 0.0])
+            a[0] += n
+            a[1] += t
+    prof.close()
+    hbm_peak, tc_peak, peak_src = measured_peaks()
+    total = sum(t for _, t in kinds.values())
+    breakdown = {k: {"launches": n, "ms_total": round(t, 4), "share": round(t / total, 4) if total else None,
+                     "us_per_launch": round(1e3 * t / n, 3) if n else None} for k, (n, t) in kinds.items() if n}
+    dom = max(breakdown, key=lambda k: breakdown[k]["ms_total"])
+    n_l, t_l = kinds[dom]
+    bound, units_l, uu = algorithmic(dom, w, pstats, n_l)
+    per_launch_s = t_l / n_l / 1e3
+    if bound == "alu":
+        achieved = units_l / per_launch_s / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / ALU_PEAK_TFLOPS, "peak_source": "derived: 152 SMs x 128 FP32 lanes x "
+                "2.07 GHz x 1.5 flop/issue (FSUB+FFMA mix)"}
+    else:
+        achieved = units_l / per_launch_s / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} hbm_gbs"}
+    roof["traffic"] = ncu_traffic(dom)
+    roof["algorithmic_per_launch"] = units_l
+    roof["launch_us"] = per_launch_s * 1e6
+
+    # --- end to end through the C ABI with host buffers ---
+    Xh = torch.from_numpy(w.X).pin_memory()
+    C0h = torch.from_numpy(w.C0).pin_memory()
+    labh = torch.empty(w.N, dtype=torch.int32).pin_memory()
+    Ch = torch.empty(w.K, w.D, dtype=torch.float32).pin_memory()
+    et, ei = [], []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k2 = kpynq.KMeans(Xh, C0h, w.G, stream=stream)
+        r = k2.fit(w.max_iter, w.tol, labh, Ch)
+        k2.close()
+        torch.cuda.synchronize()
+        if i > 0:
+            et.append(time.perf_counter() - t0)
+            ei.append(r.n_iter)
+    e2e_value = w.N * statistics.mean(ei) / statistics.mean(et)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4 + C0h.numel() * 4),
+           "d2h_bytes_per_step": int(labh.numel() * 4 + Ch.numel() * 4 + 8 + 4),
+           "ms_per_step": 1e3 * statistics.mean(et),
+           "includes": "context creation (allocation, H2D copy of X), graph recording, fit, D2H of outputs"}
+
+    if rank != 0:
+        km.close()
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, min(w.N, 1 << 18), 3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "D": w.D, "K": w.K, "G": w.G, "max_iter": w.max_iter,
+                   "tol": w.tol, "iters_per_step": statistics.mean(iters),
+                   "step": "kmeans_reset + kmeans_fit (dense iteration 0, filtered iterations, final assignment)",
+                   "l2": "flushed between steps (256 MiB write); X is 256 MiB > L2",
+                   "parallelism": f"replicas x{ws}"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": kern,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "skip_fraction": skip,
+        "plain_lloyd": {"value": lloyd_value, "ms_per_step": statistics.mean(lt), "iters": statistics.mean(li)},
+        "vs_plain_lloyd": value / lloyd_value,
+        "kernel_breakdown": breakdown,
+    }
+    print(json.dumps(line), flush=True)
+    km.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -85,10 +85,23 @@ typedef struct {
     int32_t algo;        /* KM_ALGO_* */
     int32_t grouping;    /* KM_GROUP_* */
     int32_t validate;    /* nonzero: reject X / init_centroids with NaN or Inf */
-    int32_t reserved0;
+    int32_t profile;     /* nonzero: time every kernel with CUDA events (the
+                            fit loop then runs launch by launch, not as a
+                            graph); see kmeans_get_profile */
     void *stream;        /* cudaStream_t; NULL = legacy default stream */
     int64_t reserved[6]; /* must be zero */
 } kmeans_options;
+
+/* kernel kinds reported by kmeans_get_profile */
+enum {
+    KM_KERNEL_DENSE = 0,    /* dense assignment (iteration 0, plain Lloyd) */
+    KM_KERNEL_MOVES = 1,    /* cluster sums for moved points (dense path) */
+    KM_KERNEL_FILTER = 2,   /* global filter + survivor compaction */
+    KM_KERNEL_SURVIVOR = 3, /* group/point filter + survivor distances */
+    KM_KERNEL_UPDATE = 4,   /* centroid update, drift, objective */
+    KM_KERNEL_OTHER = 5,    /* loop control, rebase, bounds export */
+    KM_KERNEL_KINDS = 6
+};
 
 /* Per-iteration statistics (all counts are for that iteration). */
 typedef struct {
@@ -137,8 +150,9 @@ KM_API int kmeans_iterate(kmeans_ctx *ctx, kmeans_iter_stats *stats);
  *   centroids K x D f32 the returned centroids
  *   objective 1 double  J of that pair (FP64)
  *   n_iter    1 int32   iterations performed by this call
- * The whole loop is replayed as one CUDA graph with a device-side loop
- * condition (no host round trip per iteration).
+ * Without profiling, the loop runs as one CUDA graph whose body repeats
+ * under a device-side loop condition set by the stop rule: no host round trip
+ * per iteration.
  */
 KM_API int kmeans_fit(kmeans_ctx *ctx, int32_t max_iter, double tol,
                       int32_t *labels, float *centroids, double *objective,
@@ -162,6 +176,22 @@ KM_API int kmeans_get_stats(kmeans_ctx *ctx, int32_t t, kmeans_iter_stats *stats
  * KM_ALGO_FILTERED after at least one iteration.
  */
 KM_API int kmeans_get_bounds(kmeans_ctx *ctx, float *u, float *lbg, float *lb);
+
+/*
+ * Restart from new initial centroids (K x D, host or device): iteration
+ * count, bounds, cluster sums, drift tables and statistics are reset; X,
+ * sizes, options, device buffers and the recorded fit graph are kept.  Makes
+ * no allocation.  Blocks until done.
+ */
+KM_API int kmeans_reset(kmeans_ctx *ctx, const float *init_centroids);
+
+/*
+ * Device time of each kernel kind since the context was created (or since
+ * the last kmeans_reset), measured with CUDA events recorded on the
+ * context's stream around every launch.  Only collected when
+ * kmeans_options.profile is set.  kind: KM_KERNEL_*.  launches / ms nullable.
+ */
+KM_API int kmeans_get_profile(kmeans_ctx *ctx, int32_t kind, int64_t *launches, double *ms);
 
 /* Number of iterations run so far on this context. */
 KM_API int kmeans_get_iteration(const kmeans_ctx *ctx, int32_t *t);

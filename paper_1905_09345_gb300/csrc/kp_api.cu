@@ -48,6 +48,17 @@ struct kmeans_ctx {
     Ctrl *ctrl_host = nullptr;  // pinned mirror of the control block
     int *flag_dev = nullptr;
     std::vector<void *> allocs;
+    long long kernels_base = 0;  // device kernel count before the last reset
+    // profiling (kmeans_options.profile): CUDA events around every launch
+    bool capturing = false;
+    double prof_ms[KM_KERNEL_KINDS] = {};
+    long long prof_n[KM_KERNEL_KINDS] = {};
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace {
@@ -122,8 +133,51 @@ float f32_dn(double x) {
     return f;
 }
 
+cudaEvent_t take_event(kmeans_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch through `fn`; when profiling (and not recording a graph), bracket it
+// with CUDA events on the context's stream.
+template <class F>
+cudaError_t timed(kmeans_ctx *c, cudaStream_t s, int kind, F fn) {
+    if (!c->opt.profile || c->capturing) return fn();
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, s);
+    if (e != cudaSuccess) return e;
+    e = fn();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(b, s);
+    if (e != cudaSuccess) return e;
+    c->pending.push_back({kind, a, b});
+    return cudaSuccess;
+}
+
+// after a stream synchronisation: fold the recorded event pairs in
+void collect_profile(kmeans_ctx *c) {
+    for (auto &q : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+            c->prof_ms[q.kind] += ms;
+            c->prof_n[q.kind] += 1;
+        }
+        c->ev_pool.push_back(q.a);
+        c->ev_pool.push_back(q.b);
+    }
+    c->pending.clear();
+}
+
 int sync_and_check(kmeans_ctx *c) {
     KP_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_profile(c);
     KP_CUDA(c, cudaMemcpy(c->ctrl_host, c->p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
     c->t_host = c->ctrl_host->t;
     c->v_host = c->ctrl_host->v;
@@ -171,12 +225,19 @@ int ensure_tables(kmeans_ctx *c, int need) {
 // One assignment (dense when `dense`, filtered otherwise), stream-ordered.
 cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool dense, bool first, int respect_done) {
     cudaError_t e;
+    const int n = c->num_sms;
     if (dense) {
-        if ((e = launch_dense_assign(p, s, first, respect_done, c->num_sms)) != cudaSuccess) return e;
-        return launch_apply_moves(p, s, first ? 1 : 0, respect_done, c->num_sms);
+        e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_dense_assign(p, s, first, respect_done, n); });
+        if (e != cudaSuccess) return e;
+        return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, first ? 1 : 0, respect_done, n); });
     }
-    if ((e = launch_filter(p, s, respect_done, c->num_sms)) != cudaSuccess) return e;
-    return launch_survivor(p, s, respect_done, c->num_sms, c->smem_optin);
+    e = timed(c, s, KM_KERNEL_FILTER, [&] { return launch_filter(p, s, respect_done, n); });
+    if (e != cudaSuccess) return e;
+    return timed(c, s, KM_KERNEL_SURVIVOR, [&] { return launch_survivor(p, s, respect_done, n, c->smem_optin); });
+}
+
+cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {
+    return timed(c, s, KM_KERNEL_UPDATE, [&] { return launch_update(p, s, final_only, respect_done); });
 }
 
 // One full iteration: assignment, then update.
@@ -184,12 +245,19 @@ cudaError_t enqueue_iteration(kmeans_ctx *c, const Params &p, cudaStream_t s, bo
     const bool dense = first || p.algo == KM_ALGO_LLOYD;
     cudaError_t e = enqueue_assign(c, p, s, dense, first, respect_done);
     if (e != cudaSuccess) return e;
-    return launch_update(p, s, 0, respect_done);
+    return enqueue_update(c, p, s, 0, respect_done);
 }
 
 // Record the fit graph: set_cond -> while(cond){ iteration } -> final
 // assignment -> objective.
+int build_fit_graph_impl(kmeans_ctx *c);
 int build_fit_graph(kmeans_ctx *c) {
+    c->capturing = true;
+    int rc = build_fit_graph_impl(c);
+    c->capturing = false;
+    return rc;
+}
+int build_fit_graph_impl(kmeans_ctx *c) {
     cudaGraph_t g = nullptr;
     KP_CUDA(c, cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -229,7 +297,7 @@ int build_fit_graph(kmeans_ctx *c) {
     pf.cond = 0;
     KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, g, &cond_node, nullptr, 1, cudaStreamCaptureModeThreadLocal));
     e = enqueue_assign(c, pf, c->cap_stream, pf.algo == KM_ALGO_LLOYD, false, 0);
-    if (e == cudaSuccess) e = launch_update(pf, c->cap_stream, 1, 0);
+    if (e == cudaSuccess) e = enqueue_update(c, pf, c->cap_stream, 1, 0);
     e2 = cudaStreamEndCapture(c->cap_stream, &g);
     KP_CUDA(c, e);
     KP_CUDA(c, e2);
@@ -409,7 +477,7 @@ KM_API int kmeans_iterate(kmeans_ctx *c, kmeans_iter_stats *stats) {
     if ((rc = ensure_tables(c, 2))) return rc;
     Params &p = c->p;
     p.tcap = c->tcap;
-    KP_CUDA(c, launch_arm(p, c->stream, 1, 0.0));
+    KP_CUDA(c, timed(c, c->stream, KM_KERNEL_OTHER, [&] { return launch_arm(p, c->stream, 1, 0.0); }));
     KP_CUDA(c, enqueue_iteration(c, p, c->stream, c->t_host == 0, 0));
     const int t = c->t_host;
     if ((rc = sync_and_check(c))) return rc;
@@ -426,11 +494,21 @@ KM_API int kmeans_fit(kmeans_ctx *c, int32_t max_iter, double tol, int32_t *labe
     if ((rc = ensure_tables(c, max_iter + 2))) return rc;
     Params &p = c->p;
     p.tcap = c->tcap;
-    KP_CUDA(c, launch_arm(p, c->stream, max_iter, tol));
+    KP_CUDA(c, timed(c, c->stream, KM_KERNEL_OTHER, [&] { return launch_arm(p, c->stream, max_iter, tol); }));
     if (c->t_host == 0 && max_iter == 0) {
         // nothing to iterate and no bounds yet: a dense assignment to C^0
         KP_CUDA(c, enqueue_assign(c, p, c->stream, true, true, 0));
-        KP_CUDA(c, launch_update(p, c->stream, 1, 0));
+        KP_CUDA(c, enqueue_update(c, p, c->stream, 1, 0));
+    } else if (c->opt.profile) {
+        // launch by launch, reading the stop rule back after each iteration
+        if (c->t_host == 0) KP_CUDA(c, enqueue_iteration(c, p, c->stream, true, 1));
+        for (;;) {
+            if ((rc = sync_and_check(c))) return rc;
+            if (c->ctrl_host->done) break;
+            KP_CUDA(c, enqueue_iteration(c, p, c->stream, false, 1));
+        }
+        KP_CUDA(c, enqueue_assign(c, p, c->stream, p.algo == KM_ALGO_LLOYD, false, 0));
+        KP_CUDA(c, enqueue_update(c, p, c->stream, 1, 0));
     } else {
         if (!c->graph_exec && (rc = build_fit_graph(c))) return rc;
         if (c->t_host == 0) KP_CUDA(c, enqueue_iteration(c, p, c->stream, true, 1));
@@ -514,7 +592,44 @@ KM_API int kmeans_get_bounds(kmeans_ctx *c, float *u, float *lbg, float *lb) {
 
 KM_API int kmeans_get_kernel_count(const kmeans_ctx *c, int64_t *n) {
     if (!c || !n) return KM_EINVAL;
-    *n = (int64_t)c->ctrl_host->kernels;
+    *n = (int64_t)(c->kernels_base + (long long)c->ctrl_host->kernels);
+    return KM_OK;
+}
+
+KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!init_centroids) return set_err(c, KM_EINVAL, "init_centroids is NULL");
+    DeviceGuard dg(c->dev);
+    Params &p = c->p;
+    cudaStream_t s = c->stream;
+    if ((rc = sync_and_check(c))) return rc;
+    c->kernels_base += (long long)c->ctrl_host->kernels;
+    KP_CUDA(c, cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)p.D * 4, (size_t)p.D * 4, p.K,
+                                 cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaMemsetAsync(p.S, 0, (size_t)p.K * p.D * 8, s));
+    KP_CUDA(c, cudaMemsetAsync(p.Q, 0, (size_t)p.K * 8, s));
+    KP_CUDA(c, cudaMemsetAsync(p.cnt, 0, (size_t)p.K * 8, s));
+    KP_CUDA(c, cudaMemsetAsync(p.Dc, 0, (size_t)c->tcap * p.K * 4, s));
+    KP_CUDA(c, cudaMemsetAsync(p.Dg, 0, (size_t)c->tcap * p.Gp * 4, s));
+    KP_CUDA(c, cudaMemsetAsync(p.Dm, 0, (size_t)c->tcap * 4, s));
+    KP_CUDA(c, cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
+    KP_CUDA(c, cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * kStatsCap, s));
+    KP_CUDA(c, cudaStreamSynchronize(s));
+    memset(c->ctrl_host, 0, sizeof(Ctrl));
+    c->t_host = 0;
+    c->v_host = 0;
+    for (int k = 0; k < KM_KERNEL_KINDS; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    return KM_OK;
+}
+
+KM_API int kmeans_get_profile(kmeans_ctx *c, int32_t kind, int64_t *launches, double *ms) {
+    if (!c || kind < 0 || kind >= KM_KERNEL_KINDS) return KM_EINVAL;
+    if (launches) *launches = c->prof_n[kind];
+    if (ms) *ms = c->prof_ms[kind];
     return KM_OK;
 }
 
@@ -530,6 +645,11 @@ KM_API void kmeans_destroy(kmeans_ctx *c) {
     if (c->stream || c->cap_stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    for (auto &q : c->pending) {
+        c->ev_pool.push_back(q.a);
+        c->ev_pool.push_back(q.b);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void *q : c->allocs) cudaFree(q);
     if (c->ctrl_host) cudaFreeHost(c->ctrl_host);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libkpynq.so")
 KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ESTATE = 0, -1, -2, -3, -4, -5
 KM_ALGO_FILTERED, KM_ALGO_LLOYD = 0, 1
 KM_GROUP_CONTIGUOUS = 0
+KM_KERNEL_DENSE, KM_KERNEL_MOVES, KM_KERNEL_FILTER, KM_KERNEL_SURVIVOR, KM_KERNEL_UPDATE, KM_KERNEL_OTHER = range(6)
+KERNEL_KIND_NAMES = ["dense_assign", "apply_moves", "filter", "survivor", "update", "other"]
 STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ENOMEM", -3: "KM_ECUDA", -4: "KM_ETIMEOUT",
                 -5: "KM_ESTATE"}
 
@@ -30,7 +32,7 @@ class KMeansError(RuntimeError):
 
 class kmeans_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("grouping", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("reserved", ctypes.c_int64 * 6)]
 
 
@@ -75,6 +77,10 @@ def lib():
         L.kmeans_get_iteration.restype = ctypes.c_int
         L.kmeans_get_kernel_count.argtypes = [vp, ctypes.POINTER(i64)]
         L.kmeans_get_kernel_count.restype = ctypes.c_int
+        L.kmeans_reset.argtypes = [vp, vp]
+        L.kmeans_reset.restype = ctypes.c_int
+        L.kmeans_get_profile.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+        L.kmeans_get_profile.restype = ctypes.c_int
         L.kmeans_destroy.argtypes = [vp]
         L.kmeans_destroy.restype = None
         L.kmeans_last_error.argtypes = [vp]
@@ -174,6 +180,18 @@ def kmeans_get_kernel_count(ctx) -> int:
     return n.value
 
 
+def kmeans_reset(ctx, init_centroids) -> None:
+    _check(lib().kmeans_reset(ctx, _addr(init_centroids)), ctx)
+
+
+def kmeans_get_profile(ctx, kind: int):
+    """Returns ``(launches, total_ms)`` for one KM_KERNEL_* kind."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(lib().kmeans_get_profile(ctx, kind, ctypes.byref(n), ctypes.byref(ms)), ctx)
+    return n.value, ms.value
+
+
 def kmeans_destroy(ctx) -> None:
     if ctx:
         lib().kmeans_destroy(ctx)
@@ -204,12 +222,14 @@ class KMeans:
     NumPy arrays, float32, row-major.  A CUDA ``X`` is borrowed (kept alive by
     this object)."""
 
-    def __init__(self, X, C0, G: int, *, algo: int = KM_ALGO_FILTERED, stream=None, validate: bool = False):
+    def __init__(self, X, C0, G: int, *, algo: int = KM_ALGO_FILTERED, stream=None, validate: bool = False,
+                 profile: bool = False):
         N, D = X.shape
         K = C0.shape[0]
         opt = kmeans_default_options()
         opt.algo = algo
         opt.validate = int(validate)
+        opt.profile = int(profile)
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else stream.cuda_stream
         self._keep = (X, C0)
@@ -227,14 +247,27 @@ class KMeans:
         except Exception:
             pass
 
+    def reset(self, C0):
+        """Restart from new initial centroids (no allocation)."""
+        self._keep = (self._keep[0], C0)
+        kmeans_reset(self.ctx, C0)
+
+    def profile(self) -> dict:
+        """Per kernel kind: (launches, total device ms)."""
+        return {KERNEL_KIND_NAMES[k]: kmeans_get_profile(self.ctx, k) for k in range(len(KERNEL_KIND_NAMES))}
+
     def iterate(self) -> dict:
         return kmeans_iterate(self.ctx)
 
-    def fit(self, max_iter: int, tol: float = 0.0, labels=None, centroids=None) -> FitResult:
+    def fit(self, max_iter: int, tol: float = 0.0, labels=None, centroids=None, with_stats: bool = True) -> FitResult:
         t0 = kmeans_get_iteration(self.ctx)
         n_iter, J = kmeans_fit(self.ctx, max_iter, tol, labels, centroids)
-        stats = [kmeans_get_stats(self.ctx, t) for t in range(t0, t0 + n_iter)]
+        stats = self.stats(t0, t0 + n_iter) if with_stats else None
         return FitResult(labels, centroids, J, n_iter, stats)
+
+    def stats(self, t0: int, t1: int) -> list:
+        """Per-iteration statistics of iterations t0 .. t1-1."""
+        return [kmeans_get_stats(self.ctx, t) for t in range(t0, t1)]
 
     def labels(self, out):
         kmeans_get_labels(self.ctx, out)
