@@ -196,6 +196,41 @@ KM_API int kmeans_get_profile(kmeans_ctx *ctx, int32_t kind, int64_t *launches, 
 /* Number of iterations run so far on this context. */
 KM_API int kmeans_get_iteration(const kmeans_ctx *ctx, int32_t *t);
 
+/*
+ * One plain-Lloyd iteration that allocates nothing.  The paper has no
+ * counterpart: this entry point is for callers that may not allocate device
+ * memory at all -- a host framework that owns every byte of device memory
+ * through its own pool, a latency-critical loop in which cudaMalloc/cudaFree
+ * would synchronise the device, or a deployment that must reserve all memory
+ * at start-up.
+ *
+ * From centroids C (K x D) it assigns every point of X (N x D) to its nearest
+ * centroid (exact, ties to the lowest index) into labels[N], writes the
+ * updated centroids (cluster means, an empty cluster keeps its centroid) to
+ * C_new (K x D) and J(labels, C) to *objective (FP64): the same results as
+ * kmeans_iterate on a KM_ALGO_LLOYD context at the same centroids.  Every
+ * pointer must be device memory of the current device; the work is ordered on
+ * `stream` (cudaStream_t, NULL = legacy default) and the call returns without
+ * waiting for it.
+ *
+ * Scratch: the cluster sums, counts, a padded copy of C and the control block
+ * live in one file-scope static device array of about 1.6 MB, which every GPU
+ * that loads the library holds until the process exits.  Hence the limits
+ * K <= KM_NOALLOC_MAX_K and D <= KM_NOALLOC_MAX_D (larger sizes: KM_EINVAL).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and clears what
+ * it accumulates into, so calls that overlap on the GPU (on different
+ * streams, or from threads without ordering) race and give wrong results.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  Errors:
+ * KM_EINVAL, KM_ECUDA; the message is kmeans_last_error(NULL).
+ */
+#define KM_NOALLOC_MAX_K 1024
+#define KM_NOALLOC_MAX_D 128
+KM_API int kmeans_lloyd_step_noalloc(const float *X, int64_t N, int32_t D, const float *C,
+                                     int32_t K, int32_t *labels, float *C_new,
+                                     double *objective, void *stream);
+
 /* Free the context and everything it allocated.  NULL is a no-op. */
 KM_API void kmeans_destroy(kmeans_ctx *ctx);
 

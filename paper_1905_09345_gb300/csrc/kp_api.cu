@@ -27,6 +27,10 @@ using namespace kp;
 
 static thread_local char g_init_error[512] = "";
 
+namespace kp {
+void set_thread_error(const char *msg) { snprintf(g_init_error, sizeof(g_init_error), "%s", msg); }
+}  // namespace kp
+
 struct kmeans_ctx {
     int dev = 0;
     int num_sms = 0;

@@ -253,6 +253,7 @@ __device__ __forceinline__ float drift_m(const Params &p, int v, int w) {
 // host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------
 void count_launch();
+void set_thread_error(const char *msg);  // message for kmeans_last_error(NULL)
 int dense_dp(int D);  // register tile width used for D (0 = generic path)
 
 cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);

@@ -81,6 +81,8 @@ def lib():
         L.kmeans_reset.restype = ctypes.c_int
         L.kmeans_get_profile.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
         L.kmeans_get_profile.restype = ctypes.c_int
+        L.kmeans_lloyd_step_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, vp]
+        L.kmeans_lloyd_step_noalloc.restype = ctypes.c_int
         L.kmeans_destroy.argtypes = [vp]
         L.kmeans_destroy.restype = None
         L.kmeans_last_error.argtypes = [vp]
@@ -190,6 +192,18 @@ def kmeans_get_profile(ctx, kind: int):
     ms = ctypes.c_double()
     _check(lib().kmeans_get_profile(ctx, kind, ctypes.byref(n), ctypes.byref(ms)), ctx)
     return n.value, ms.value
+
+
+KM_NOALLOC_MAX_K = 1024
+KM_NOALLOC_MAX_D = 128
+
+
+def kmeans_lloyd_step_noalloc(X, N: int, D: int, C, K: int, labels, C_new, objective, stream=None) -> None:
+    """One plain-Lloyd iteration with no allocation (device arrays only;
+    stream-ordered, does not wait).  See include/kpynq.h."""
+    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().kmeans_lloyd_step_noalloc(_addr(X), N, D, _addr(C), K, _addr(labels), _addr(C_new),
+                                           _addr(objective), st), None)
 
 
 def kmeans_destroy(ctx) -> None:
