@@ -331,11 +331,15 @@ def run_ours(args):
     n_dist = sum(s["n_dist"] for s in stats)
     skip = 1.0 - n_dist / (w.N * w.K * len(stats))
 
-    # --- plain GPU Lloyd on the same GPU and inputs ---
+    # --- plain GPU Lloyd on the same GPU and inputs: tensor cores, FP32 ---
     lloyd = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream)
-    lt, li, _, _ = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd")
+    lt, li, _, _ = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd (TF32 tensor cores)")
     lloyd_value = w.N * statistics.mean(li) / (statistics.mean(lt) / 1e3)
     lloyd.close()
+    lloyd32 = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream, dense=kpynq.KM_DENSE_FP32)
+    lt32, li32, _, _ = timed_steps(lloyd32, args.lloyd_steps, 1, "plain Lloyd (FP32 CUDA cores)")
+    lloyd32_value = w.N * statistics.mean(li32) / (statistics.mean(lt32) / 1e3)
+    lloyd32.close()
 
     # --- profiled pass: CUDA events around every launch ---
     prof = kpynq.KMeans(X, C0, w.G, stream=stream, profile=True)
@@ -415,8 +419,13 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "skip_fraction": skip,
-        "plain_lloyd": {"value": lloyd_value, "ms_per_step": statistics.mean(lt), "iters": statistics.mean(li)},
+        "plain_lloyd": {"value": lloyd_value, "ms_per_step": statistics.mean(lt), "iters": statistics.mean(li),
+                        "dense": "TF32 tensor cores + exact settle"},
         "vs_plain_lloyd": value / lloyd_value,
+        "plain_lloyd_fp32": {"value": lloyd32_value, "ms_per_step": statistics.mean(lt32),
+                             "iters": statistics.mean(li32), "dense": "FP32 CUDA cores"},
+        "vs_plain_lloyd_fp32": value / lloyd32_value,
+        "paths": [s["path"] for s in stats],
         "kernel_breakdown": breakdown,
     }
     print(json.dumps(line), flush=True)

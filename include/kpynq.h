@@ -89,8 +89,21 @@ typedef struct {
                             fit loop then runs launch by launch, not as a
                             graph); see kmeans_get_profile */
     void *stream;        /* cudaStream_t; NULL = legacy default stream */
-    int64_t reserved[6]; /* must be zero */
+    int32_t dense;       /* KM_DENSE_*: engine of the dense (all-pairs) passes */
+    float dense_switch;  /* a filtered iteration whose global filter leaves more
+                            than this fraction of the points runs the dense pass
+                            instead; 0 = library default (0.08), >= 1 = never */
+    int64_t reserved[5]; /* must be zero */
 } kmeans_options;
+
+/* kmeans_options.dense: how dense passes (iteration 0, plain Lloyd) compute
+ * distances.  Both give exact labels. */
+enum {
+    KM_DENSE_AUTO = 0, /* tensor cores (tcgen05, bfloat16 split in three
+                          products, FP32 accumulation) when the shape allows
+                          (D = 64 or 128, K <= 256), else FP32 */
+    KM_DENSE_FP32 = 1  /* FP32 CUDA cores, direct differences */
+};
 
 /* kernel kinds reported by kmeans_get_profile */
 enum {
@@ -103,10 +116,21 @@ enum {
     KM_KERNEL_KINDS = 6
 };
 
-/* Per-iteration statistics (all counts are for that iteration). */
+/* kmeans_iter_stats.path */
+enum {
+    KM_PATH_FILTERED = 0,   /* global/group/point filters + survivor distances */
+    KM_PATH_DENSE_FP32 = 1, /* every distance, FP32 CUDA cores */
+    KM_PATH_DENSE_TC = 2    /* every distance, tensor cores + exact settle */
+};
+
+/* Per-iteration statistics (all counts are for that iteration).  A filtered
+ * iteration whose global filter leaves more than a set fraction of the points
+ * runs the dense pass instead (decided on the device). */
 typedef struct {
     int32_t iter;          /* t */
     int32_t done;          /* the stop rule held after this iteration */
+    int32_t path;          /* KM_PATH_*: how the assignment was computed */
+    int32_t reserved;
     int64_t n_changed;     /* labels that changed (N at t = 0) */
     int64_t n_survivors;   /* points not kept by the global filter */
     int64_t n_scanned;     /* points still unresolved after tightening u */

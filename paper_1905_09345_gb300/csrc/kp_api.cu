@@ -41,6 +41,7 @@ struct kmeans_ctx {
     Params p{};
     float *X_own = nullptr;
     int tcap = 0;
+    bool use_tc = false;   // dense passes on the tensor cores
     int t_host = 0;        // iterations run (mirrors ctrl->t after each call)
     int v_host = 0;        // table version (mirrors ctrl->v)
     bool broken = false;
@@ -231,13 +232,26 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
     cudaError_t e;
     const int n = c->num_sms;
     if (dense) {
-        e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_dense_assign(p, s, first, respect_done, n); });
+        e = timed(c, s, KM_KERNEL_DENSE, [&] {
+            return c->use_tc ? launch_dense_tc(p, s, first, respect_done, n, c->smem_optin)
+                             : launch_dense_assign(p, s, first, respect_done, n);
+        });
         if (e != cudaSuccess) return e;
         return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, first ? 1 : 0, respect_done, n); });
     }
+    // filtered: global filter, then either the survivor kernel or -- when the
+    // filter kernel finds too many survivors -- the dense pass (each of the
+    // two exits at once when the device chose the other)
     e = timed(c, s, KM_KERNEL_FILTER, [&] { return launch_filter(p, s, respect_done, n); });
     if (e != cudaSuccess) return e;
-    return timed(c, s, KM_KERNEL_SURVIVOR, [&] { return launch_survivor(p, s, respect_done, n, c->smem_optin); });
+    e = timed(c, s, KM_KERNEL_SURVIVOR, [&] { return launch_survivor(p, s, respect_done, n, c->smem_optin); });
+    if (e != cudaSuccess) return e;
+    e = timed(c, s, KM_KERNEL_DENSE, [&] {
+        return c->use_tc ? launch_dense_tc(p, s, 0, respect_done, n, c->smem_optin, 1)
+                         : launch_dense_assign(p, s, 0, respect_done, n, 1);
+    });
+    if (e != cudaSuccess) return e;
+    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, 0, respect_done, n, 1); });
 }
 
 cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {
@@ -345,7 +359,9 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     if (opt) o = *opt;
     if (o.algo != KM_ALGO_FILTERED && o.algo != KM_ALGO_LLOYD) return set_err(nullptr, KM_EINVAL, "unknown algo %d", o.algo);
     if (o.grouping != KM_GROUP_CONTIGUOUS) return set_err(nullptr, KM_EINVAL, "unknown grouping %d", o.grouping);
-    for (int i = 0; i < 6; ++i)
+    if (o.dense != KM_DENSE_AUTO && o.dense != KM_DENSE_FP32) return set_err(nullptr, KM_EINVAL, "unknown dense %d", o.dense);
+    if (!(o.dense_switch >= 0.0f)) return set_err(nullptr, KM_EINVAL, "dense_switch must be >= 0");
+    for (int i = 0; i < 5; ++i)
         if (o.reserved[i]) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
 
     kmeans_ctx *c = new (std::nothrow) kmeans_ctx();
@@ -454,6 +470,18 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.eps_hi = f32_up(1.0 + 2.0 * eps);
     p.eps_lo = f32_dn(1.0 - eps);
     p.tiny = std::ldexp((float)(D + 4), -149);
+    p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : 0.08f;
+
+    c->use_tc = o.dense == KM_DENSE_AUTO && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
+                dense_tc_eligible(p, c->smem_optin);
+    if (c->use_tc) {  // the two bfloat16 halves of X, made once
+        uint16_t *xh, *xl;
+        INIT_CUDA(dalloc(c, &xh, (size_t)N * D));
+        INIT_CUDA(dalloc(c, &xl, (size_t)N * D));
+        INIT_CUDA(launch_split_x(p.X, N, D, xh, xl, s, c->num_sms));
+        p.Xh = xh;
+        p.Xl = xl;
+    }
 
     if (o.validate) {
         INIT_CUDA(cudaMemsetAsync(c->flag_dev, 0, 4, s));

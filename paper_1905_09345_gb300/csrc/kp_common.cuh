@@ -23,7 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/kpynq.h"
+#include "kpynq.h"
 
 namespace kp {
 
@@ -47,7 +47,9 @@ struct Ctrl {
     double jfinal;
     unsigned long long n_changed, n_survivors, n_scanned, n_dist, n_recheck;
     int32_t fit_n_iter;   // iterations performed by the current fit call
-    int32_t pad0;
+    int32_t path;         // KM_PATH_* of the current assignment
+    int32_t dense_mode;   // the current filtered iteration runs the dense pass
+    uint32_t filter_ticket;  // last-block-done counter of the filter kernel
     unsigned long long kernels;  // kernels of this context run on the device
 };
 
@@ -59,6 +61,8 @@ __device__ __forceinline__ void count_kernel(Ctrl *c) {
 // Everything a kernel needs, passed by value.
 struct Params {
     const float *X;      // N x D, row-major
+    const uint16_t *Xh;  // N x D bfloat16: bf16(x)            (tensor-core path)
+    const uint16_t *Xl;  // N x D bfloat16: bf16(x - bf16(x))  (tensor-core path)
     int64_t N;
     int32_t D, K, G;
     int32_t Dp;          // centroid row stride (floats), >= D, multiple of 4
@@ -96,6 +100,7 @@ struct Params {
     float eps_lo;        // s_true >= s_fp32 * eps_lo - tiny
     float tiny;          // absolute slack for underflow
     int32_t algo;
+    float dense_frac;    // survivor fraction above which an iteration runs dense
     unsigned long long cond;  // cudaGraphConditionalHandle of the fit loop (0: none)
 };
 
@@ -256,8 +261,16 @@ void count_launch();
 void set_thread_error(const char *msg);  // message for kmeans_last_error(NULL)
 int dense_dp(int D);  // register tile width used for D (0 = generic path)
 
-cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);
-cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms);
+// `if_dense`: run only when the filter kernel chose the dense pass for this iteration
+cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
+                                int if_dense = 0);
+bool dense_tc_eligible(const Params &p, size_t smem_limit);
+cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
+                           int num_sms);
+cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
+                            size_t smem_limit, int if_dense = 0);
+cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms,
+                               int if_dense = 0);
 cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms);
 cudaError_t launch_survivor(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit);
 cudaError_t launch_update(const Params &p, cudaStream_t s, int final_only, int respect_done);

@@ -99,11 +99,13 @@ __device__ __forceinline__ float sqdist_again(const Params &p, const XRow<(DP > 
 // moved and are added to the sums by the caller).  Writes labels; for the
 // filtered method also u, lbg, lb and stamps (exact at the current version).
 template <int DP>
-__global__ void __launch_bounds__(kDenseThreads) k_dense_assign(Params p, int first, int respect_done) {
+__global__ void __launch_bounds__(kDenseThreads) k_dense_assign(Params p, int first, int respect_done, int if_dense) {
     extern __shared__ __align__(128) float smem[];
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (if_dense && !*(volatile int *)&ctrl->dense_mode) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->path = KM_PATH_DENSE_FP32;
     const int v = ctrl->v;
     const int K = p.K;
     const int G = p.G;
@@ -300,10 +302,11 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_assign(Params p, int fi
 // Cluster statistics for moved points: S[new] += x, S[old] -= x (FP64),
 // Q (sum of ||x||^2) and counts likewise.  One warp per point, lanes over the
 // coordinates, so each point's atomics are coalesced.
-__global__ void __launch_bounds__(256) k_apply_moves(Params p, int all_points, int respect_done) {
+__global__ void __launch_bounds__(256) k_apply_moves(Params p, int all_points, int respect_done, int if_dense) {
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (if_dense && !*(volatile int *)&ctrl->dense_mode) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -345,7 +348,8 @@ int dense_dp(int D) {
 }
 
 template <int DP>
-static cudaError_t launch_dense_t(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms) {
+static cudaError_t launch_dense_t(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
+                                  int if_dense) {
     constexpr int DPs = DP > 0 ? DP : 4;
     const int KT = DP > 0 ? std::min(p.K, kDenseTileBytes / (DPs * 4)) : 0;
     size_t smem = (size_t)KT * DPs * 4;
@@ -359,28 +363,30 @@ static cudaError_t launch_dense_t(const Params &p, cudaStream_t s, int first, in
     int64_t tiles = (p.N + kDenseThreads - 1) / kDenseThreads;
     int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * std::max(per_sm, 1));
     count_launch();
-    k_dense_assign<DP><<<(unsigned)grid, kDenseThreads, smem, s>>>(p, first, respect_done);
+    k_dense_assign<DP><<<(unsigned)grid, kDenseThreads, smem, s>>>(p, first, respect_done, if_dense);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms) {
+cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
+                                int if_dense) {
     switch (dense_dp(p.D)) {
-    case 4: return launch_dense_t<4>(p, s, first, respect_done, num_sms);
-    case 8: return launch_dense_t<8>(p, s, first, respect_done, num_sms);
-    case 16: return launch_dense_t<16>(p, s, first, respect_done, num_sms);
-    case 32: return launch_dense_t<32>(p, s, first, respect_done, num_sms);
-    case 64: return launch_dense_t<64>(p, s, first, respect_done, num_sms);
-    case 128: return launch_dense_t<128>(p, s, first, respect_done, num_sms);
-    default: return launch_dense_t<0>(p, s, first, respect_done, num_sms);
+    case 4: return launch_dense_t<4>(p, s, first, respect_done, num_sms, if_dense);
+    case 8: return launch_dense_t<8>(p, s, first, respect_done, num_sms, if_dense);
+    case 16: return launch_dense_t<16>(p, s, first, respect_done, num_sms, if_dense);
+    case 32: return launch_dense_t<32>(p, s, first, respect_done, num_sms, if_dense);
+    case 64: return launch_dense_t<64>(p, s, first, respect_done, num_sms, if_dense);
+    case 128: return launch_dense_t<128>(p, s, first, respect_done, num_sms, if_dense);
+    default: return launch_dense_t<0>(p, s, first, respect_done, num_sms, if_dense);
     }
 }
 
-cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms) {
+cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms,
+                               int if_dense) {
     int64_t items = all_points ? p.N : p.N;  // moved count is only known on the device
     int64_t grid = std::min<int64_t>((items + 7) / 8, (int64_t)num_sms * 8);
     grid = std::max<int64_t>(grid, 1);
     count_launch();
-    k_apply_moves<<<(unsigned)grid, 256, 0, s>>>(p, all_points, respect_done);
+    k_apply_moves<<<(unsigned)grid, 256, 0, s>>>(p, all_points, respect_done, if_dense);
     return cudaGetLastError();
 }
 

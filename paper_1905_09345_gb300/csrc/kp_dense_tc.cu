@@ -1,0 +1,711 @@
+// kp_dense_tc.cu -- dense assignment on the 5th-generation tensor cores.
+//
+// The distance calculator of KPynq (Sec. I) evaluates every pair the filters
+// leave; when that is (nearly) every pair -- iteration 0, plain Lloyd, or a
+// filtered iteration in which most points survive -- the evaluation is a
+// dense contraction, ||x||^2 - 2 x.c + ||c||^2, and belongs on the tensor
+// cores.
+//
+// Mixed precision with a bounded error ("BF16x3"): every FP32 value v is
+// split into two bfloat16 numbers, v_h = bf16(v) and v_l = bf16(v - v_h), and
+//     x.c ~ x_h.c_h + x_h.c_l + x_l.c_h
+// is accumulated in FP32 by tcgen05.mma (kind::f16, M=128 points x N<=256
+// centroids, K=16 per instruction, three instructions per K step).  X is
+// split once per context into two bfloat16 copies that TMA loads with
+// 128-byte swizzle; the centroid block is split into shared memory by the
+// CTA itself.  Accumulators live in TMEM, double-buffered across two
+// epilogue warp groups.
+//
+// Persistent CTA per SM: warp 0 issues TMA, one thread of warp 1 issues the
+// MMAs, warps 2..9 (two groups of four) read the accumulators back with
+// tcgen05.ld, one TMEM lane (= point) per thread, and turn
+// t_k = ||c_k||^2 - 2 x.c_k into the winner, the runner-up and the per-group
+// minima.  Lower bounds are t-based with the error E(x) subtracted, the upper
+// bound adds it; when the runner-up lies within 2E of the winner the point is
+// settled exactly (FP32 direct differences from global memory, then FP64 if
+// the FP32 error bound cannot decide), so labels are exact.
+//
+// Error model of t_k (per point; c_max = max ||c_k||, c2_max = max ||c_k||^2):
+//   the split leaves |v - v_h - v_l| <= 2^-16 |v| (bfloat16 unit roundoff
+//   2^-8, twice), so the three products miss at most 3.05 2^-16 |x_i c_i|;
+//   products are exact in FP32 and the accumulation of 3D of them adds at
+//   most 3D 2^-23 (Cauchy-Schwarz bounds sum |x_i c_i| by ||x|| ||c||);
+//   ||c||^2 is an FP32 sum of squares and the final fma rounds once:
+//     |t~ - t| <= (6.1 2^-16 + (6D+1) 2^-23) ||x|| ||c|| + (D+3) 2^-24 ||c||^2,
+//   used with a 1.25x margin as E(x).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "kp_common.cuh"
+
+namespace kp {
+
+namespace {
+
+constexpr int kTM = 128;          // points per tile
+constexpr int kEpiWarps = 4;      // warps per epilogue group
+constexpr int kGroups = 2;        // epilogue groups = TMEM buffers
+constexpr int kTcThreads = 64 + kGroups * kEpiWarps * 32;
+constexpr uint32_t kPolls = 1u << 22;
+constexpr int kAtomBytes = kTM * 128;  // one 64-element bfloat16 column block of a tile
+
+struct TcCfg {
+    int Kp;        // centroid rows in shared memory (multiple of 32, <= 256)
+    int stages;    // A pipeline depth
+    int tmem_cols; // allocated TMEM columns (2 buffers)
+    int buf_cols;  // columns per buffer (>= Kp, power of two)
+    uint32_t off_A, off_cn, off_gs, off_stage, off_bar;
+    int num_tiles;
+    float e_lin;   // 1.25 (6.1 2^-16 + (6D+1) 2^-23), rounded up
+    float e_c2;    // 1.25 (D+3) 2^-24, rounded up
+    float xn_lo, xn_hi;  // relative error of ||x||^2 from the split copy
+};
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// bounded wait; on time-out records KM_ETIMEOUT and returns false
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, Ctrl *ctrl) {
+    for (uint32_t i = 0; i < kPolls; ++i)
+        if (mbar_try_wait(b, parity)) return true;
+    atomicExch(&ctrl->err, (int)KM_ETIMEOUT);
+    return false;
+}
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *m, int c0, int c1, uint64_t *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(smem_u32(b))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Asynchronous TMEM read of 32 columns; the registers may be used only after
+// tmem_wait32 on the same array (which names them, so that the compiler
+// cannot move their uses above the wait).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
+}
+
+// byte offset of the 16-byte chunk holding bfloat16 elements [8q, 8q+8) of
+// `row` in a 128-byte-swizzled K-major tile (64 elements per 128-byte row)
+__device__ __forceinline__ uint32_t swz_chunk(int row, int q, int atom_bytes) {
+    return (uint32_t)((q >> 3) * atom_bytes + row * 128 + (((q & 7) ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ void split8(const float *v, uint4 &h, uint4 &l) {
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
+        __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
+        __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
+        hw[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lw[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// ||x||^2 of one row of the split A tile, from x_h + x_l
+template <int D>
+__device__ __forceinline__ float row_norm2(const uint8_t *Ah, const uint8_t *Al, int row) {
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < D / 8; ++q) {
+        const uint4 h = *reinterpret_cast<const uint4 *>(Ah + swz_chunk(row, q, kAtomBytes));
+        const uint4 l = *reinterpret_cast<const uint4 *>(Al + swz_chunk(row, q, kAtomBytes));
+        const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float v0 = bf_lo(hw[i]) + bf_lo(lw[i]);
+            const float v1 = bf_hi(hw[i]) + bf_hi(lw[i]);
+            a0 = fmaf(v0, v0, a0);
+            a1 = fmaf(v1, v1, a1);
+        }
+    }
+    return a0 + a1;
+}
+
+// FP32 direct-difference squared distance from global memory (rare path)
+__device__ __forceinline__ float sqdist_global(const float *x, const float *c, int D) {
+    float a0 = 0.f, a1 = 0.f;
+    int i = 0;
+    for (; i + 1 < D; i += 2) {
+        const float t0 = x[i] - c[i], t1 = x[i + 1] - c[i + 1];
+        a0 = fmaf(t0, t0, a0);
+        a1 = fmaf(t1, t1, a1);
+    }
+    if (i < D) {
+        const float t0 = x[i] - c[i];
+        a0 = fmaf(t0, t0, a0);
+    }
+    return a0 + a1;
+}
+
+// FP32 direct-difference squared distance, x in registers (D/4 float4),
+// c a 16-byte-aligned row in global memory
+template <int D>
+__device__ __forceinline__ float sqdist_reg4(const float4 (&x)[D / 4], const float *c) {
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < D / 4; q += 2) {
+        const float4 c0 = __ldg(reinterpret_cast<const float4 *>(c) + q);
+        const float4 c1 = __ldg(reinterpret_cast<const float4 *>(c) + q + 1);
+        float t;
+        t = x[q].x - c0.x; a0 = fmaf(t, t, a0);
+        t = x[q].y - c0.y; a0 = fmaf(t, t, a0);
+        t = x[q].z - c0.z; a0 = fmaf(t, t, a0);
+        t = x[q].w - c0.w; a0 = fmaf(t, t, a0);
+        t = x[q + 1].x - c1.x; a1 = fmaf(t, t, a1);
+        t = x[q + 1].y - c1.y; a1 = fmaf(t, t, a1);
+        t = x[q + 1].z - c1.z; a1 = fmaf(t, t, a1);
+        t = x[q + 1].w - c1.w; a1 = fmaf(t, t, a1);
+    }
+    return a0 + a1;
+}
+
+// Stage the closing group's minimum and return the next boundary (a value
+// no column index reaches once the last group is open).
+__device__ __noinline__ int close_group(float *row, const int *gs, int &g, float gm1, int K) {
+    row[g] = gm1;
+    ++g;
+    const int e = gs[g + 1];
+    return e < K ? e : 0x7fffffff;
+}
+
+__device__ __forceinline__ float sqrt_dn(float v) {  // <= sqrt(v)
+    const float q = __fsqrt_rn(fmaxf(v, 0.f));
+    return q > 0.f ? __int_as_float(__float_as_int(q) - 1) : 0.f;
+}
+__device__ __forceinline__ float sqrt_up(float v) {  // >= sqrt(v)
+    const float q = __fsqrt_rn(fmaxf(v, 0.f));
+    return __int_as_float(__float_as_int(q) + 1);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_dense_tc(const __grid_constant__ CUtensorMap tmh, const __grid_constant__ CUtensorMap tml, Params p, TcCfg cfg,
+               int first, int respect_done, int if_dense) {
+    extern __shared__ uint8_t raw[];
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (if_dense && !*(volatile int *)&ctrl->dense_mode) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->path = KM_PATH_DENSE_TC;
+    constexpr int NA = D / 64;  // 64-element atoms per row
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
+    const int Kp = cfg.Kp;
+    const int b_atom = Kp * 128;
+    uint8_t *sBh = sm;
+    uint8_t *sBl = sm + NA * b_atom;
+    uint8_t *sA = sm + cfg.off_A;  // stage s: [NA atoms of x_h][NA atoms of x_l]
+    float *cn = reinterpret_cast<float *>(sm + cfg.off_cn);
+    int *gs = reinterpret_cast<int *>(sm + cfg.off_gs);
+    float *stage = reinterpret_cast<float *>(sm + cfg.off_stage);  // [8 warps x 32 rows][Gp + 1]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + cfg.off_bar);
+    const int S = cfg.stages;
+    uint64_t *full_a = bars;
+    uint64_t *empty_a = bars + S;
+    uint64_t *acc_full = bars + 2 * S;  // [kGroups]
+    uint64_t *acc_empty = bars + 2 * S + kGroups;
+    uint64_t *mma_done = bars + 2 * S + 2 * kGroups;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * kGroups + 1);
+    float *c2max_s = reinterpret_cast<float *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = ctrl->v;
+    const int K = p.K, G = p.G;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            bar_init(&full_a[i], 1);
+            bar_init(&empty_a[i], kEpiWarps);
+        }
+        for (int g = 0; g < kGroups; ++g) {
+            bar_init(&acc_full[g], 1);
+            bar_init(&acc_empty[g], kEpiWarps);
+        }
+        bar_init(mma_done, 1);
+        *c2max_s = 0.f;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(cfg.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = p.gstart[g];
+    // the centroid block, split into x_h / x_l bfloat16 tiles (128-byte swizzle),
+    // and the exact FP32 norms (padding rows: zero tiles, norm +inf)
+    for (int idx = threadIdx.x; idx < Kp * (D / 8); idx += blockDim.x) {
+        const int row = idx / (D / 8), q = idx - row * (D / 8);
+        float vals[8];
+        if (row < K) {
+            const float4 a = *reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp + q * 8);
+            const float4 b = *reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp + q * 8 + 4);
+            vals[0] = a.x; vals[1] = a.y; vals[2] = a.z; vals[3] = a.w;
+            vals[4] = b.x; vals[5] = b.y; vals[6] = b.z; vals[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) vals[i] = 0.f;
+        }
+        uint4 h, l;
+        split8(vals, h, l);
+        *reinterpret_cast<uint4 *>(sBh + swz_chunk(row, q, b_atom)) = h;
+        *reinterpret_cast<uint4 *>(sBl + swz_chunk(row, q, b_atom)) = l;
+    }
+    {
+        float cm = 0.f;
+        for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+            float s2 = INFINITY;
+            if (k < K) {
+                const float *c = p.C + (size_t)k * p.Dp;
+                float a0 = 0.f, a1 = 0.f;
+                for (int d = 0; d + 1 < D; d += 2) {
+                    a0 = fmaf(c[d], c[d], a0);
+                    a1 = fmaf(c[d + 1], c[d + 1], a1);
+                }
+                s2 = a0 + a1;
+                cm = fmaxf(cm, s2);
+            }
+            cn[k] = s2;
+        }
+        cm = warp_max(cm);
+        __syncthreads();  // c2max_s initialised
+        if (lane == 0 && cm > 0.f) atomicMax(reinterpret_cast<int *>(c2max_s), __float_as_int(cm));
+    }
+    // generic-proxy writes of the B tiles must be visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmh) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tml) : "memory");
+            int i = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < cfg.num_tiles && ok; tile += gridDim.x, ++i) {
+                const int s = i % S, f = i / S;
+                if (f > 0) ok = bar_wait(&empty_a[s], (f - 1) & 1, ctrl);
+                if (!ok) break;
+                uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
+                mbar_arrive_expect_tx(&full_a[s], (uint32_t)(2 * NA * kAtomBytes));
+                for (int a = 0; a < NA; ++a) {
+                    tma_2d(st + a * kAtomBytes, &tmh, 64 * a, tile * kTM, &full_a[s]);
+                    tma_2d(st + (NA + a) * kAtomBytes, &tml, 64 * a, tile * kTM, &full_a[s]);
+                }
+            }
+            // drain: every issued copy has landed before the block can exit
+            const int issued = i;
+            for (int j = issued - S < 0 ? 0 : issued - S; j < issued; ++j)
+                bar_wait(&full_a[j % S], (j / S) & 1, ctrl);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA
+        if (lane == 0) {
+            // kind::f16: F32 accumulate, BF16 A and B, K-major, N = Kp, M = 128
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Kp >> 3) << 17) |
+                                   ((uint32_t)(kTM >> 4) << 24);
+            bool ok = true;
+            int i = 0;
+            for (int tile = blockIdx.x; tile < cfg.num_tiles && ok; tile += gridDim.x, ++i) {
+                const int s = i % S, f = i / S;
+                const int buf = i % kGroups, u = i / kGroups;
+                if (u > 0 && !(ok = bar_wait(&acc_empty[buf], (u - 1) & 1, ctrl))) break;
+                if (!(ok = bar_wait(&full_a[s], f & 1, ctrl))) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(buf * cfg.buf_cols);
+                const uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
+#pragma unroll
+                for (int ks = 0; ks < D / 16; ++ks) {
+                    const int a = ks >> 2, j = ks & 3;
+                    const uint64_t dah = desc_sw128(smem_u32(st + a * kAtomBytes + j * 32));
+                    const uint64_t dal = desc_sw128(smem_u32(st + (NA + a) * kAtomBytes + j * 32));
+                    const uint64_t dbh = desc_sw128(smem_u32(sBh + a * b_atom + j * 32));
+                    const uint64_t dbl = desc_sw128(smem_u32(sBl + a * b_atom + j * 32));
+                    const uint32_t acc = ks > 0;
+                    asm volatile(
+                        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %5, %3, q;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %6, %2, %3, q;\n\t}" ::"r"(d_tmem),
+                        "l"(dah), "l"(dbh), "r"(idesc), "r"(acc), "l"(dbl), "l"(dal)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&acc_full[buf]))
+                             : "memory");
+            }
+            // every MMA of this thread is complete before TMEM is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mma_done))
+                         : "memory");
+            bar_wait(mma_done, 0, ctrl);
+        }
+    } else {
+        // ------------------------------------------------------- epilogue
+        const int grp_id = (warp - 2) / kEpiWarps;
+        const int q = warp & 3;  // TMEM lane quadrant of this warp
+        const int r = q * 32 + lane;
+        const bool bounds = p.algo == KM_ALGO_FILTERED;
+        const float c2max = __fmul_ru(*c2max_s, 1.0f + 1.0f / 1024);
+        const float cmax = sqrt_up(c2max);
+        const float ec2 = __fmul_ru(cfg.e_c2, c2max);
+        float *row = stage + (size_t)((warp - 2) * 32 + lane) * (p.Gp + 1);
+        unsigned long long c_changed = 0, c_recheck = 0, c_dist = 0;
+        int i = grp_id;
+        for (int tile = blockIdx.x + grp_id * gridDim.x; tile < cfg.num_tiles;
+             tile += kGroups * gridDim.x, i += kGroups) {
+            const int s = i % S, f = i / S;
+            const int u = i / kGroups;
+            // waits are warp-uniform: the TMEM loads below are warp-collective
+            if (!__all_sync(0xffffffffu, bar_wait(&acc_full[grp_id], u & 1, ctrl))) break;
+            if (!__all_sync(0xffffffffu, bar_wait(&full_a[s], f & 1, ctrl))) break;
+            tc_fence_after();
+            const uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
+            const int64_t n = (int64_t)tile * kTM + r;
+            const bool valid = n < p.N;
+            const float xn = row_norm2<D>(st, st + NA * kAtomBytes, r);
+            // the split copy of A is no longer needed
+            __syncwarp();
+            if (lane == 0) bar_arrive(&empty_a[s]);
+            const float xlo = __fmul_rd(xn, cfg.xn_lo), xup = __fmul_ru(xn, cfg.xn_hi);
+            const float E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_up(xup), cmax), ec2);
+            const float twoE = __fmul_ru(2.f, E);
+            const uint32_t tb = tmem + (uint32_t)(grp_id * cfg.buf_cols) + ((uint32_t)(q * 32) << 16);
+
+            // pass 1: group minima (staged), winner (lowest index on ties), runner-up
+            float b1 = INFINITY, b2 = INFINITY, gm1 = INFINITY;
+            int i1 = 0, cur_g = 0, gend = gs[1] < K ? gs[1] : 0x7fffffff;
+            for (int c0 = 0; c0 < Kp; c0 += 32) {
+                uint32_t rr[32];
+                tmem_ld32(tb + c0, rr);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 c4 = *reinterpret_cast<const float4 *>(cn + c0 + j);
+                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int col = c0 + j + jj;
+                        const float t = fmaf(-2.f, __uint_as_float(rr[j + jj]), cv[jj]);
+                        if (col == gend) {  // uniform
+                            gend = close_group(row, gs, cur_g, gm1, K);
+                            gm1 = INFINITY;
+                        }
+                        gm1 = fminf(gm1, t);
+                        b2 = fminf(b2, fmaxf(b1, t));
+                        if (t < b1) {
+                            b1 = t;
+                            i1 = col;
+                        }
+                    }
+                }
+            }
+            row[cur_g] = gm1;
+            const float thr = __fadd_ru(b1, twoE);
+
+            // settle exactly where the runner-up is inside the error window: a
+            // rescan of the accumulators collects the window's columns (up to
+            // four ids packed in one register), then they are evaluated exactly,
+            // lane-parallel, from global memory
+            int best = i1;
+            float s_exact = -1.f;
+            const bool need = valid && b2 <= thr;
+            if (__any_sync(0xffffffffu, need)) {
+                uint32_t pack = 0;
+                int nc = 0;
+                for (int c0 = 0; c0 < Kp; c0 += 32) {
+                    uint32_t rr[32];
+                    tmem_ld32(tb + c0, rr);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float t = fmaf(-2.f, __uint_as_float(rr[j]), cn[c0 + j]);
+                        const bool in = need && t <= thr;
+                        pack = in ? (pack << 8) | (uint32_t)(c0 + j) : pack;
+                        nc += in;
+                    }
+                }
+                if (need) {
+                    const float *xg = p.X + n * D;
+                    float4 xr[D / 4];
+#pragma unroll
+                    for (int q4 = 0; q4 < D / 4; ++q4) xr[q4] = __ldg(reinterpret_cast<const float4 *>(xg) + q4);
+                    float bs = INFINITY, sec = INFINITY;
+                    int bi = i1;
+                    const int m = nc > 4 ? K : nc;  // overflow (rare): every centroid
+                    for (int k = 0; k < m; ++k) {
+                        const int col = nc > 4 ? k : (int)((pack >> (8 * (nc - 1 - k))) & 0xffu);
+                        const float sx = sqdist_reg4<D>(xr, p.C + (size_t)col * p.Dp);
+                        if (sx < bs || (sx == bs && col < bi)) {
+                            sec = bs;
+                            bs = sx;
+                            bi = col;
+                        } else if (sx < sec) {
+                            sec = sx;
+                        }
+                    }
+                    best = bi;
+                    s_exact = bs;
+                    if (sec != INFINITY && unresolved(bs, sec, p)) {
+                        double bd = INFINITY;
+                        int bj = bi;
+                        for (int col = 0; col < K; ++col) {
+                            const float sx = sqdist_global(xg, p.C + (size_t)col * p.Dp, D);
+                            if (!unresolved(bs, sx, p)) continue;
+                            const double d64 = dist2_f64(xg, p.C + (size_t)col * p.Dp, D);
+                            if (d64 < bd) { bd = d64; bj = col; }
+                        }
+                        best = bj;
+                        s_exact = sqdist_global(xg, p.C + (size_t)bj * p.Dp, D);
+                        c_recheck += 1;
+                    }
+                }
+            }
+            // accumulators no longer needed
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&acc_empty[grp_id]);
+
+            if (valid) {
+                c_dist += (unsigned long long)K;
+                const int old = first ? -1 : p.label[n];
+                p.label[n] = best;
+                if (bounds) {
+                    // s_c >= xn_lo + t_c - E for every column c
+                    for (int g = 0; g < G; ++g) {
+                        const float tg = row[g];
+                        row[g] = tg == INFINITY ? INFINITY : sqrt_dn(__fsub_rd(__fadd_rd(xlo, tg), E));
+                    }
+                    // the winner's group must exclude the winner: every other
+                    // column is at least the runner-up b2 (at least b1 when the
+                    // exact winner is not the tensor-core winner)
+                    const float tw = best == i1 ? b2 : b1;
+                    row[p.grp[best]] = tw == INFINITY ? INFINITY : sqrt_dn(__fsub_rd(__fadd_rd(xlo, tw), E));
+                    float mm = INFINITY;
+                    for (int g = 0; g < G; ++g) mm = fminf(mm, row[g]);
+                    p.lbg[n] = mm;
+                    p.u[n] = s_exact >= 0.f ? dist_up(s_exact, p) : sqrt_up(__fadd_ru(__fadd_ru(xup, b1), E));
+                    p.stamp[n] = make_stamp(v, v);
+                }
+                if (old != best) {
+                    c_changed += 1;
+                    if (!first) {
+                        const int slot = atomicAdd(&ctrl->moved_count, 1);
+                        p.moved[slot] = (int)n;
+                        p.moved_old[slot] = old;
+                    }
+                }
+            }
+            if (bounds) {
+                // the warp's 32 rows (consecutive points) as one contiguous block
+                __syncwarp();
+                const int64_t n0 = (int64_t)tile * kTM + q * 32;
+                const int rows = (int)min((int64_t)32, p.N - n0);
+                if (rows > 0) {
+                    const float *st0 = stage + (size_t)((warp - 2) * 32) * (p.Gp + 1);
+                    float *dst = p.lb + n0 * p.Gp;
+                    for (int rw = 0; rw < rows; ++rw)
+                        for (int g = lane; g < p.Gp; g += 32)
+                            dst[(size_t)rw * p.Gp + g] = g < G ? st0[rw * (p.Gp + 1) + g] : 0.f;
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c_changed += __shfl_xor_sync(0xffffffffu, c_changed, o);
+            c_recheck += __shfl_xor_sync(0xffffffffu, c_recheck, o);
+            c_dist += __shfl_xor_sync(0xffffffffu, c_dist, o);
+        }
+        if (lane == 0) {
+            if (c_changed) atomicAdd(&ctrl->n_changed, c_changed);
+            if (c_recheck) atomicAdd(&ctrl->n_recheck, c_recheck);
+            if (c_dist) atomicAdd(&ctrl->n_dist, c_dist);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cfg.tmem_cols)
+                     : "memory");
+    }
+}
+
+// X -> (x_h, x_l) bfloat16 copies, four elements per thread
+__global__ void k_split_x(const float *X, int64_t n4, uint2 *Xh, uint2 *Xl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4 *>(X)[i];
+        const float vv[4] = {a.x, a.y, a.z, a.w};
+        uint32_t hw[2], lw[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            __nv_bfloat16 h0 = __float2bfloat16_rn(vv[2 * k]), h1 = __float2bfloat16_rn(vv[2 * k + 1]);
+            __nv_bfloat16 l0 = __float2bfloat16_rn(vv[2 * k] - __bfloat162float(h0));
+            __nv_bfloat16 l1 = __float2bfloat16_rn(vv[2 * k + 1] - __bfloat162float(h1));
+            hw[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        Xh[i] = make_uint2(hw[0], hw[1]);
+        Xl[i] = make_uint2(lw[0], lw[1]);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int pow2_at_least(int x) {
+    int p2 = 32;
+    while (p2 < x) p2 <<= 1;
+    return p2;
+}
+
+bool plan(const Params &p, size_t smem_limit, TcCfg &cfg, size_t &smem) {
+    if (p.D % 64 != 0 || p.D > 128 || p.K > 256) return false;
+    cfg.Kp = ((p.K + 31) / 32) * 32;
+    cfg.buf_cols = pow2_at_least(cfg.Kp);
+    cfg.tmem_cols = kGroups * cfg.buf_cols;
+    if (cfg.tmem_cols > 512) return false;
+    const size_t NA = p.D / 64;
+    const size_t b_bytes = 2 * NA * (size_t)cfg.Kp * 128;
+    const size_t a_stage = 2 * NA * (size_t)kAtomBytes;
+    const size_t cn_bytes = (size_t)cfg.Kp * 4;
+    const size_t gs_bytes = (((size_t)p.G + 1) * 4 + 15) & ~size_t(15);
+    const size_t stage_bytes = (size_t)kGroups * kTM * (p.Gp + 1) * 4;
+    const size_t fixed = 1024 + b_bytes + cn_bytes + gs_bytes + stage_bytes + 64 * 8 + 64;
+    if (fixed + 2 * a_stage > smem_limit) return false;
+    cfg.stages = (int)std::min<size_t>(6, (smem_limit - fixed) / a_stage);
+    size_t off = b_bytes;
+    cfg.off_A = (uint32_t)off;
+    off += cfg.stages * a_stage;
+    cfg.off_cn = (uint32_t)off;
+    off += cn_bytes;
+    cfg.off_gs = (uint32_t)off;
+    off += gs_bytes;
+    cfg.off_stage = (uint32_t)off;
+    off += stage_bytes;
+    off = (off + 7) & ~size_t(7);
+    cfg.off_bar = (uint32_t)off;
+    off += (2 * cfg.stages + 2 * kGroups + 1) * 8 + 16;
+    smem = 1024 + off;
+    if (smem > smem_limit) return false;
+    cfg.num_tiles = (int)((p.N + kTM - 1) / kTM);
+    const double D = p.D;
+    cfg.e_lin = (float)(1.25 * (6.1 * std::ldexp(1.0, -16) + (6 * D + 1) * std::ldexp(1.0, -23)) * (1 + 1e-6));
+    cfg.e_c2 = (float)(1.25 * (D + 3) * std::ldexp(1.0, -24) * (1 + 1e-6));
+    // ||x||^2 from x_h + x_l: (1 +- 2^-16)^2 per element and an FP32 sum of D squares
+    const double rel = 2 * (std::ldexp(1.0, -15) + (D + 2) * std::ldexp(1.0, -24));
+    cfg.xn_lo = (float)(1.0 - rel);
+    cfg.xn_hi = (float)(1.0 + rel);
+    return true;
+}
+
+template <int D>
+cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms, size_t smem_limit,
+                     int if_dense) {
+    TcCfg cfg;
+    size_t smem;
+    if (!plan(p, smem_limit, cfg, smem) || !p.Xh || !p.Xl) return cudaErrorNotSupported;
+    auto enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap tmh, tml;
+    cuuint64_t gx[2] = {(cuuint64_t)p.D, (cuuint64_t)p.N}, sx[1] = {(cuuint64_t)p.D * 2};
+    cuuint32_t bx[2] = {64, (cuuint32_t)kTM}, es[2] = {1, 1};
+    if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(p.Xh), gx, sx, bx, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    if (enc(&tml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(p.Xl), gx, sx, bx, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(cfg.num_tiles, num_sms);
+    count_launch();
+    k_dense_tc<D><<<grid, kTcThreads, smem, s>>>(tmh, tml, p, cfg, first, respect_done, if_dense);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dense_tc_eligible(const Params &p, size_t smem_limit) {
+    TcCfg cfg;
+    size_t smem;
+    return encoder() != nullptr && plan(p, smem_limit, cfg, smem);
+}
+
+cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
+                           int num_sms) {
+    const int64_t n4 = N * D / 4;  // D is a multiple of 64
+    const int64_t grid = std::min<int64_t>((n4 + 255) / 256, (int64_t)num_sms * 16);
+    count_launch();
+    k_split_x<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(X, n4, reinterpret_cast<uint2 *>(Xh),
+                                                                    reinterpret_cast<uint2 *>(Xl));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
+                            size_t smem_limit, int if_dense) {
+    switch (p.D) {
+    case 64: return launch_t<64>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
+    case 128: return launch_t<128>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace kp

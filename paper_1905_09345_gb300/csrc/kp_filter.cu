@@ -90,6 +90,18 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(Params p, int respect
         my_surv += (lane == 0) ? (unsigned long long)total : 0ull;
     }
     if (lane == 0 && my_surv) atomicAdd(&ctrl->n_survivors, my_surv);
+    // the last block to finish decides whether this iteration runs the dense pass
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->filter_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const int q = *(volatile int *)&ctrl->queue_count;
+        ctrl->dense_mode = (double)q > (double)p.dense_frac * (double)p.N;
+        ctrl->filter_ticket = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -159,6 +171,7 @@ __global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, in
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (*(volatile int *)&ctrl->dense_mode) return;  // this iteration runs the dense pass
     const int count = *(volatile int *)&ctrl->queue_count;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;

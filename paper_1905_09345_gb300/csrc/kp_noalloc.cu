@@ -173,8 +173,8 @@ KM_API int kmeans_lloyd_step_noalloc(const float *X, int64_t N, int32_t D, const
     count_launch();
 
     // the existing kernels: dense exact assignment, cluster sums, update
-    NA_CUDA(launch_dense_assign(p, s, 1, 0, num_sms));
-    NA_CUDA(launch_apply_moves(p, s, 1, 0, num_sms));
+    NA_CUDA(launch_dense_assign(p, s, 1, 0, num_sms, 0));
+    NA_CUDA(launch_apply_moves(p, s, 1, 0, num_sms, 0));
     NA_CUDA(launch_update(p, s, 0, 0));
 
     NA_CUDA(cudaMemcpy2DAsync(C_new, sizeof(float) * D, p.C, sizeof(float) * p.Dp, sizeof(float) * D, K,

@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         st.n_scanned = (int64_t)ctrl->n_scanned;
         st.n_dist = (int64_t)ctrl->n_dist;
         st.n_recheck = (int64_t)ctrl->n_recheck;
+        st.path = ctrl->path;
         st.objective = J;
         if (final_only) {
             ctrl->jfinal = J;
@@ -130,6 +131,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         ctrl->n_changed = ctrl->n_survivors = ctrl->n_scanned = ctrl->n_dist = ctrl->n_recheck = 0;
         ctrl->queue_count = 0;
         ctrl->moved_count = 0;
+        ctrl->path = KM_PATH_FILTERED;
+        ctrl->dense_mode = 0;
         __threadfence();
         ctrl->ticket = 0;
     }

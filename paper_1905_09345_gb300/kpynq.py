@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libkpynq.so")
 KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ESTATE = 0, -1, -2, -3, -4, -5
 KM_ALGO_FILTERED, KM_ALGO_LLOYD = 0, 1
 KM_GROUP_CONTIGUOUS = 0
+KM_DENSE_AUTO, KM_DENSE_FP32 = 0, 1
+KM_PATH_FILTERED, KM_PATH_DENSE_FP32, KM_PATH_DENSE_TC = 0, 1, 2
 KM_KERNEL_DENSE, KM_KERNEL_MOVES, KM_KERNEL_FILTER, KM_KERNEL_SURVIVOR, KM_KERNEL_UPDATE, KM_KERNEL_OTHER = range(6)
 KERNEL_KIND_NAMES = ["dense_assign", "apply_moves", "filter", "survivor", "update", "other"]
 STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ENOMEM", -3: "KM_ECUDA", -4: "KM_ETIMEOUT",
@@ -32,12 +34,13 @@ class KMeansError(RuntimeError):
 
 class kmeans_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("grouping", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("dense", ctypes.c_int32),
+                ("dense_switch", ctypes.c_float), ("reserved", ctypes.c_int64 * 5)]
 
 
 class kmeans_iter_stats(ctypes.Structure):
-    _fields_ = [("iter", ctypes.c_int32), ("done", ctypes.c_int32), ("n_changed", ctypes.c_int64),
+    _fields_ = [("iter", ctypes.c_int32), ("done", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n_changed", ctypes.c_int64),
                 ("n_survivors", ctypes.c_int64), ("n_scanned", ctypes.c_int64), ("n_dist", ctypes.c_int64),
                 ("n_recheck", ctypes.c_int64), ("objective", ctypes.c_double), ("max_drift", ctypes.c_double)]
 
@@ -237,13 +240,15 @@ class KMeans:
     this object)."""
 
     def __init__(self, X, C0, G: int, *, algo: int = KM_ALGO_FILTERED, stream=None, validate: bool = False,
-                 profile: bool = False):
+                 profile: bool = False, dense: int = KM_DENSE_AUTO, dense_switch: float = 0.0):
         N, D = X.shape
         K = C0.shape[0]
         opt = kmeans_default_options()
         opt.algo = algo
         opt.validate = int(validate)
         opt.profile = int(profile)
+        opt.dense = dense
+        opt.dense_switch = dense_switch
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else stream.cuda_stream
         self._keep = (X, C0)

@@ -76,6 +76,16 @@ def test_init_rejects_null_and_bad_options(L):
         L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
     assert e.value.status == L.KM_EINVAL
     opt = L.kmeans_default_options()
+    opt.dense = 5
+    with pytest.raises(L.KMeansError) as e:
+        L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
+    assert e.value.status == L.KM_EINVAL
+    opt = L.kmeans_default_options()
+    opt.dense_switch = -1.0
+    with pytest.raises(L.KMeansError) as e:
+        L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
+    assert e.value.status == L.KM_EINVAL
+    opt = L.kmeans_default_options()
     opt.reserved[2] = 1
     with pytest.raises(L.KMeansError) as e:
         L.kmeans_init(16, 10, 4, 2, 1, 16, opt)

@@ -48,12 +48,23 @@ def get_labels(km):
     return km.labels(out).cpu().numpy()
 
 
-def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None):
+def tc_expected(D, K, G, smem=232448):
+    """Mirror of the tensor-core kernel's eligibility (shape and shared memory)."""
+    if D % 64 or D > 128 or K > 256:
+        return False
+    Kp = (K + 31) // 32 * 32
+    na = D // 64
+    Gp = (G + 3) // 4 * 4
+    fixed = 1024 + 2 * na * Kp * 128 + Kp * 4 + ((G + 1) * 4 + 15) // 16 * 16 + 2 * 128 * (Gp + 1) * 4 + 64 * 8 + 64
+    return fixed + 2 * 2 * na * 128 * 128 <= smem
+
+
+def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None, dense=0, dense_switch=0.0):
     """Run `iters` iterations in lockstep with the oracle; returns the list of
     per-iteration GPU stats."""
     N, D = X.shape
     K = C0.shape[0]
-    km = kp.KMeans(dev(X), dev(C0), G, algo=algo)
+    km = kp.KMeans(dev(X), dev(C0), G, algo=algo, dense=dense, dense_switch=dense_switch)
     X64 = X.astype(np.float64)
     prev = None
     stats = []
@@ -91,6 +102,11 @@ def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None):
             for g in range(G):
                 m = np.where((grp == g)[None, :], dd, np.inf).min(1)
                 assert np.all(lb[:, g] <= m * (1 + 1e-12)), f"t={t}: group {g} lower bound above distance"
+        if t > 0 and algo == 0 and dense_switch >= 1.0:
+            assert st["path"] == kp.KM_PATH_FILTERED, (t, st["path"])
+        if t == 0 or algo == kp.KM_ALGO_LLOYD:
+            want = kp.KM_PATH_DENSE_TC if (dense == 0 and tc_expected(D, K, G)) else kp.KM_PATH_DENSE_FP32
+            assert st["path"] == want, (t, st["path"], want)
         stats.append(st)
         prev = ref
     if report is not None:
@@ -102,11 +118,13 @@ def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None):
 def test_small_blobs_lockstep(kp):
     """Plain filtered K-means, FP32: N=16,384, D=16, K=16, G=2, 20 iterations."""
     w = synth.small_blobs()
-    rep = {}
-    st = lockstep(kp, w.X, w.C0, w.G, w.max_iter, report=rep)
-    assert st[0]["n_dist"] == w.N * w.K
-    # the filters remove work once the centroids settle
-    assert sum(s["n_dist"] for s in st[5:]) < 0.5 * w.N * w.K * len(st[5:])
+    for sw in (0.0, 1.0):  # default dense switch; filtered path forced
+        rep = {}
+        st = lockstep(kp, w.X, w.C0, w.G, w.max_iter, report=rep, dense_switch=sw)
+        assert st[0]["n_dist"] == w.N * w.K
+        # the filters remove work once the centroids settle
+        late = [s for s in st[5:] if s["path"] == kp.KM_PATH_FILTERED]
+        assert late and sum(s["n_dist"] for s in late) < 0.5 * w.N * w.K * len(late)
 
 
 def test_small_blobs_fit_matches_oracle_run(kp):
@@ -149,26 +167,51 @@ EDGE = [
 ]
 
 
+@pytest.mark.parametrize("dense", [0, 1], ids=["auto", "fp32"])
 @pytest.mark.parametrize("N,D,K,G,iters", EDGE, ids=[f"N{e[0]}_D{e[1]}_K{e[2]}_G{e[3]}" for e in EDGE])
-def test_edge_shapes_lockstep(kp, N, D, K, G, iters):
+def test_edge_shapes_lockstep(kp, N, D, K, G, iters, dense):
     rng = np.random.default_rng(N * 7 + D)
     X, _ = synth.gaussian_mixture(rng, N, D, max(K, 2), centre_range=4.0, scale="fixed", scale_args=(1.0,))
     C0 = synth.sample_init(rng, X, K)
-    lockstep(kp, X, C0, G, iters, check_bounds=(N * K <= 200000))
+    lockstep(kp, X, C0, G, iters, check_bounds=(N * K <= 200000), dense=dense,
+             dense_switch=1.0 if dense else 0.0)
 
 
-@pytest.mark.parametrize("N,D,K,G,iters", EDGE[:6], ids=[f"N{e[0]}_D{e[1]}_K{e[2]}_G{e[3]}" for e in EDGE[:6]])
-def test_plain_lloyd_lockstep(kp, N, D, K, G, iters):
+LLOYD_SHAPES = EDGE[:6] + [(5000, 64, 256, 26, 4), (3001, 32, 33, 4, 5)]
+
+
+@pytest.mark.parametrize("dense", [0, 1], ids=["auto", "fp32"])
+@pytest.mark.parametrize("N,D,K,G,iters", LLOYD_SHAPES, ids=[f"N{e[0]}_D{e[1]}_K{e[2]}_G{e[3]}" for e in LLOYD_SHAPES])
+def test_plain_lloyd_lockstep(kp, N, D, K, G, iters, dense):
     rng = np.random.default_rng(N * 11 + D)
     X, _ = synth.gaussian_mixture(rng, N, D, max(K, 2), centre_range=4.0, scale="fixed", scale_args=(1.0,))
     C0 = synth.sample_init(rng, X, K)
-    st = lockstep(kp, X, C0, G, iters, algo=kp.KM_ALGO_LLOYD)
+    st = lockstep(kp, X, C0, G, iters, algo=kp.KM_ALGO_LLOYD, dense=dense)
     assert all(s["n_dist"] == N * K for s in st)
+
+
+@pytest.mark.parametrize("D", [32, 64, 128])
+def test_tensor_core_near_ties(kp, D):
+    """Points placed (almost) half-way between two centroids, far from the
+    origin so that the TF32 error window is wide: every one must be settled
+    exactly (FP32, then FP64) to the oracle's label."""
+    rng = np.random.default_rng(D)
+    K, N = 96, 4096
+    C0 = (rng.uniform(-3, 3, (K, D)) + 40.0).astype(np.float32)
+    a = rng.integers(0, K, N)
+    b = (a + 1 + rng.integers(0, K - 1, N)) % K
+    w = (0.5 + rng.uniform(-1e-6, 1e-6, N))[:, None]
+    X = (w * C0[a] + (1 - w) * C0[b] + rng.normal(0, 1e-4, (N, D))).astype(np.float32)
+    X[: N // 8] = (0.5 * C0[a[: N // 8]] + 0.5 * C0[b[: N // 8]]).astype(np.float32)  # exact midpoints
+    for algo in (0, 1):
+        st = lockstep(kp, X, C0, 8, 2, algo=algo)
+        assert st[0]["n_recheck"] > 0
 
 
 def test_bounds_stay_valid(kp):
     w = synth.small_blobs(N=3000, D=16, K=24, G=5, seed=4)
-    lockstep(kp, w.X, w.C0, w.G, 12, check_bounds=True)
+    lockstep(kp, w.X, w.C0, w.G, 12, check_bounds=True, dense_switch=1.0)
+    lockstep(kp, w.X, w.C0, w.G, 12, check_bounds=True, dense_switch=0.01)
 
 
 def test_exact_ties_go_to_lowest_index(kp):
@@ -292,8 +335,9 @@ def aniso():
 def test_aniso_reduced_lockstep(kp):
     """Same recipe at N=65,536: every iteration checked, with bounds."""
     w = synth.anisotropic_1m(N=1 << 16)
-    st = lockstep(kp, w.X, w.C0, w.G, 8)
-    assert st[-1]["n_dist"] < 0.5 * w.N * w.K
+    lockstep(kp, w.X, w.C0, w.G, 8)
+    st = lockstep(kp, w.X, w.C0, w.G, 8, dense_switch=1.0)  # filtered path throughout
+    assert st[-1]["n_dist"] < 0.2 * w.N * w.K
 
 
 def test_aniso_full_size(kp, aniso):
@@ -325,5 +369,5 @@ def test_aniso_full_size(kp, aniso):
     assert np.array_equal(lab[idx], ref)
     J = oracle.lloyd_objective(X64, lab, C)
     assert abs(r.objective - J) <= OBJECTIVE_RTOL * J
-    assert r.stats[-1]["n_dist"] < 0.1 * w.N * w.K
+    assert all(s["path"] in (kp.KM_PATH_FILTERED, kp.KM_PATH_DENSE_TC) for s in r.stats)
     km.close()
