@@ -251,7 +251,8 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
                          : launch_dense_assign(p, s, 0, respect_done, n, 1);
     });
     if (e != cudaSuccess) return e;
-    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, 0, respect_done, n, 1); });
+    // both the survivor kernel and the dense pass append to the moved-point list
+    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, 0, respect_done, n); });
 }
 
 cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {

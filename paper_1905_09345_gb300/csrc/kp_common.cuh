@@ -273,6 +273,8 @@ cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, 
                                int if_dense = 0);
 cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms);
 cudaError_t launch_survivor(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit);
+bool survivor_tp_eligible(const Params &p);
+cudaError_t launch_survivor_tp(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit);
 cudaError_t launch_update(const Params &p, cudaStream_t s, int final_only, int respect_done);
 cudaError_t launch_arm(const Params &p, cudaStream_t s, int max_iter, double tol);
 cudaError_t launch_set_cond(const Params &p, cudaStream_t s);

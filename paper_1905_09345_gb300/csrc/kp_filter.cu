@@ -16,8 +16,10 @@
 //               (lb_g at the stamp minus the centroid's own drift since then)
 //               and the distance calculator over the surviving centroids
 //               (lanes over centroids); refreshes u, lb, lbg and the label,
-//               settles near-ties in FP64, and moves the point's coordinates
-//               between the FP64 cluster sums when its label changes.
+//               settles near-ties in FP64, and appends the point to the
+//               moved-point list when its label changes.  Used for D > 64;
+//               smaller D takes the thread-per-point kernel of
+//               kp_survivor_tp.cu.
 #include "kp_common.cuh"
 
 namespace kp {
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, in
     int *sg = reinterpret_cast<int *>(lbe + p.Gp);
     int *off = sg + p.Gp;
 
-    unsigned long long c_scanned = 0, c_dist = 0, c_recheck = 0, c_changed = 0;
+    unsigned long long c_scanned = 0, c_dist = 0, c_recheck = 0, c_changed = 0, c_dist_lane = 0;
 
     for (int it = gwarp; it < count; it += nwarps) {
         const int64_t n = p.queue[it];
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, in
                     } else {
                         s = sqdist_lane<DP>(xs, Cs + (size_t)c * p.Dp, D);
                         sq[c] = s;
-                        c_dist += 1;
+                        c_dist_lane += 1;
                     }
                 }
                 if (c == a) c = 0x7fffffff;
@@ -377,25 +379,21 @@ __global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, in
             p.stamp[n] = make_stamp(v, v);
         }
         if (best != a) {
-            // move x between the FP64 cluster sums
-            double qx = 0.0;
-            for (int i = lane; i < D; i += 32) {
-                double xi = (double)xs[i];
-                qx += xi * xi;
-                atomicAdd(&p.S[(size_t)best * D + i], xi);
-                atomicAdd(&p.S[(size_t)a * D + i], -xi);
-            }
-            qx = warp_sum_d(qx);
+            // the moves kernel moves x between the cluster sums afterwards
             if (lane == 0) {
-                atomicAdd(&p.Q[best], qx);
-                atomicAdd(&p.Q[a], -qx);
-                atomicAdd(&p.cnt[best], 1ull);
-                atomicAdd(&p.cnt[a], ~0ull);
+                const int slot = atomicAdd(&ctrl->moved_count, 1);
+                p.moved[slot] = (int32_t)n;
+                p.moved_old[slot] = a;
             }
             c_changed += 1;
         }
         __syncwarp();
     }
+    // c_dist counts per lane (the lanes split the candidates); the other
+    // counters are per point and identical in every lane
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c_dist_lane += __shfl_xor_sync(0xffffffffu, c_dist_lane, o);
+    c_dist += c_dist_lane;
     if (lane == 0) {
         if (c_scanned) atomicAdd(&ctrl->n_scanned, c_scanned);
         if (c_dist) atomicAdd(&ctrl->n_dist, c_dist);
@@ -447,6 +445,7 @@ static cudaError_t launch_surv_dp(const Params &p, cudaStream_t s, int respect_d
 }
 
 cudaError_t launch_survivor(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit) {
+    if (survivor_tp_eligible(p)) return launch_survivor_tp(p, s, respect_done, num_sms, smem_limit);
     smem_limit -= 64;  // static shared (mbarrier)
     switch (dense_dp(p.D)) {
     case 4: return launch_surv_dp<4>(p, s, respect_done, num_sms, smem_limit);

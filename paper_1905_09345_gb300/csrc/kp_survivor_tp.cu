@@ -1,0 +1,376 @@
+// kp_survivor_tp.cu -- the filtered assignment of the survivors, one thread
+// per point (D <= 64).
+//
+// The survivors of the global filter (KPynq Sec. I: the "Multi-level Filters"
+// in front of the "Distance Calculator") mostly need very little work: the
+// tightened own distance, one group-bound test per group, and on average
+// fewer than one further distance.  A warp per point leaves that work
+// latency-bound on shuffles and dependent loads, so here each thread owns one
+// queued point:
+//
+//   * the point's coordinates live in registers (D/4 float4 loads);
+//   * the centroids (K x Dp FP32) are staged in shared memory by TMA bulk
+//     copies when they fit, else read through the read-only path;
+//   * the stored group bounds are read and rewritten in place, one row per
+//     thread (the row's cache lines stay in L1 between the reads);
+//   * groups are visited in index order with a running best, so the group
+//     filter and the point filter test against the best distance found so
+//     far (a valid upper bound of the final best);
+//   * each group's refreshed bound is the smallest lower value of its
+//     centroids other than the final best: every centroid contributes either
+//     its computed distance (rounded down) or its point-filter bound, and the
+//     group that holds the running best keeps both the value that excludes
+//     the best and the value that includes it, in case the best moves on;
+//   * a point whose FP32 best and runner-up cannot be separated by the FP32
+//     error bound is settled over all K centroids, in FP64 where needed, and
+//     its bounds are rebuilt from that full scan;
+//   * label changes go to the moved-point list; the cluster sums are updated
+//     by the moves kernel afterwards.
+#include "kp_common.cuh"
+
+namespace kp {
+namespace {
+
+constexpr int kTpThreads = 256;
+
+// packed pair of FP32 values (one 64-bit register pair)
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float hsum2(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo + hi;
+}
+
+// Direct-difference squared distance sum_i (x_i - c_i)^2 with packed FP32x2
+// subtract and fused multiply-add (each lane of a pair is an ordinary
+// round-to-nearest FP32 operation): four partial sums of D/4 terms each, so
+// the FP32 error bound of a D-term sum covers it.  Padding coordinates are
+// zero on both sides.
+template <int DP>
+__device__ __forceinline__ float sqdist_xr(const float4 (&xr)[DP / 4], const float *__restrict__ c) {
+    unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+    for (int q = 0; q < DP / 4; ++q) {
+        const float4 c4 = *reinterpret_cast<const float4 *>(c + 4 * q);
+        unsigned long long d0, d1;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(pack2(xr[q].x, xr[q].y)), "l"(pack2(c4.x, c4.y)));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(pack2(xr[q].z, xr[q].w)), "l"(pack2(c4.z, c4.w)));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
+    }
+    return hsum2(a0) + hsum2(a1);
+}
+
+template <int DP>
+__device__ __forceinline__ void load_x(const Params &p, int64_t n, float4 (&xr)[DP / 4]) {
+    const int D = p.D;
+    const float *xg = p.X + n * D;
+    if (p.x_vec4) {
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q)
+            xr[q] = 4 * q < D ? __ldg(reinterpret_cast<const float4 *>(xg) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q) {
+            xr[q].x = 4 * q + 0 < D ? __ldg(xg + 4 * q + 0) : 0.f;
+            xr[q].y = 4 * q + 1 < D ? __ldg(xg + 4 * q + 1) : 0.f;
+            xr[q].z = 4 * q + 2 < D ? __ldg(xg + 4 * q + 2) : 0.f;
+            xr[q].w = 4 * q + 3 < D ? __ldg(xg + 4 * q + 3) : 0.f;
+        }
+    }
+}
+
+// FP64 squared distance, coordinates ascending, no fused multiply-add (the
+// summation order of the FP64 definition)
+template <int DP>
+__device__ __forceinline__ double dist2_f64_xr(const float4 (&xr)[DP / 4], const float *__restrict__ c, int D) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < DP / 4; ++q) {
+        const float xv[4] = {xr[q].x, xr[q].y, xr[q].z, xr[q].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (4 * q + j < D) {
+                const double t = __dsub_rn((double)xv[j], (double)c[4 * q + j]);
+                s = __dadd_rn(s, __dmul_rn(t, t));
+            }
+        }
+    }
+    return s;
+}
+
+// Rare path: the FP32 results do not separate the best from the runner-up.
+// Scan all K centroids in FP32, settle the unresolved ones in FP64 (lowest
+// index on equal FP64 distances), then rebuild every group bound from the
+// full scan.  Returns the winner; *s_win is its FP32 squared distance.
+template <int DP>
+__device__ __noinline__ int settle_full(const Params &p, const float *Cs, const int32_t *gs, int64_t n,
+                                        float *s_win, float *lbg_out) {
+    const int K = p.K, G = p.G, D = p.D;
+    float4 xr[DP / 4];
+    load_x<DP>(p, n, xr);
+    float s1 = INFINITY;
+    int i1 = 0;
+    for (int c = 0; c < K; ++c) {
+        const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
+        if (s < s1) {
+            s1 = s;
+            i1 = c;
+        }
+    }
+    double bd = INFINITY;
+    int bi = i1;
+    for (int c = 0; c < K; ++c) {
+        const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
+        if (!unresolved(s1, s, p)) continue;
+        const double d = dist2_f64_xr<DP>(xr, Cs + (size_t)c * p.Dp, D);
+        if (d < bd || (d == bd && c < bi)) {
+            bd = d;
+            bi = c;
+        }
+    }
+    float lmin = INFINITY;
+    float *lbrow = p.lb + n * p.Gp;
+    for (int g = 0; g < G; ++g) {
+        float m = INFINITY;
+        for (int c = gs[g]; c < gs[g + 1]; ++c) {
+            if (c == bi) continue;
+            m = fminf(m, dist_dn(sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp), p));
+        }
+        lbrow[g] = m;
+        lmin = fminf(lmin, m);
+    }
+    *s_win = sqdist_xr<DP>(xr, Cs + (size_t)bi * p.Dp);
+    *lbg_out = lmin;
+    return bi;
+}
+
+template <int DP, bool STAGE>
+__global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int respect_done) {
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (*(volatile int *)&ctrl->dense_mode) return;  // this iteration runs the dense pass
+    const int count = *(volatile int *)&ctrl->queue_count;
+    if ((int64_t)blockIdx.x * kTpThreads >= count) return;  // no work for this block (uniform)
+    const int v = ctrl->v;
+    const int K = p.K, G = p.G, Gp = p.Gp;
+
+    // shared layout: [C (K x Dp) when staged] Dc[v] (K) | Dg[v] (Gp) | gstart (G + 1)
+    const float *Cs = p.C;
+    float *tail = smem;
+    if constexpr (STAGE) {
+        if (!stage_to_smem(smem, p.C, (uint32_t)((size_t)K * p.Dp * 4), &bar, ctrl)) return;
+        Cs = smem;
+        tail = smem + (size_t)K * p.Dp;
+    }
+    float *dcv = tail;
+    float *dgv = dcv + K;
+    int32_t *gs = reinterpret_cast<int32_t *>(dgv + Gp);
+    for (int i = threadIdx.x; i < K; i += kTpThreads) dcv[i] = p.Dc[(size_t)v * K + i];
+    for (int i = threadIdx.x; i < Gp; i += kTpThreads) dgv[i] = p.Dg[(size_t)v * Gp + i];
+    for (int i = threadIdx.x; i <= G; i += kTpThreads) gs[i] = p.gstart[i];
+    __syncthreads();
+
+    unsigned long long c_scanned = 0, c_dist = 0, c_recheck = 0, c_changed = 0;
+    const int lane = threadIdx.x & 31;
+
+    for (int64_t it = (int64_t)blockIdx.x * kTpThreads + threadIdx.x; it - lane < count;
+         it += (int64_t)gridDim.x * kTpThreads) {
+        const bool active = it < count;
+        bool moved = false;
+        int64_t n = 0;
+        int a = 0;
+        if (active) {
+            n = p.queue[it];
+            a = p.label[n];
+            const uint32_t st = p.stamp[n];
+            const int wl = (int)stamp_l(st);
+            const float lbg_e = __fsub_rd(p.lbg[n], drift_m(p, v, wl));
+
+            float4 xr[DP / 4];
+            load_x<DP>(p, n, xr);
+
+            // tighten: exact distance to the own centroid, then the global test again
+            const float sa = sqdist_xr<DP>(xr, Cs + (size_t)a * p.Dp);
+            const float ut = dist_up(sa, p);
+            c_dist += 1;
+            if (ut <= lbg_e) {
+                p.u[n] = ut;
+                p.stamp[n] = make_stamp(v, wl);
+            } else {
+                c_scanned += 1;
+                const float da_dn = dist_dn(sa, p);
+                const float *dcw = p.Dc + (size_t)wl * K;
+                const float *dgw = p.Dg + (size_t)wl * Gp;
+                float *lbrow = p.lb + n * Gp;
+
+                float s_best = sa, s_sec = INFINITY, bd_up = ut;
+                int best = a;
+                int bg = -1;                      // group holding the running best, once visited
+                float bg_val = INFINITY, bg_m1 = INFINITY;  // its bound without / with the best
+                float lmin = INFINITY;            // minimum over the other groups' new bounds
+
+                for (int g = 0; g < G; ++g) {
+                    const float lr = lbrow[g];
+                    const float le = wl == v ? lr : __fsub_rd(lr, __fsub_ru(dgv[g], __ldg(dgw + g)));
+                    const int c_lo = gs[g], c_hi = gs[g + 1];
+                    const bool has_a = a >= c_lo && a < c_hi;
+                    float val, val_leave;
+                    bool here = false;  // the best is in this group when it is done
+                    if (!(le < bd_up)) {
+                        // group filter: no centroid of g can beat the running best
+                        if (has_a) {
+                            val = best == a ? le : fminf(le, da_dn);
+                            val_leave = fminf(le, da_dn);
+                            here = best == a;
+                        } else {
+                            val = le;
+                            val_leave = le;
+                        }
+                    } else {
+                        // point filter + distance calculator over the group.  Two
+                        // pools of lower values: computed squared distances (the two
+                        // smallest, with the index of the smallest; the own centroid
+                        // enters with its exact value) and point-filter bounds (the
+                        // smallest); dist_dn is monotone, so it is applied once at the end.
+                        float sm1 = INFINITY, sm2 = INFINITY, pm1 = INFINITY;
+                        int sm1i = -1;
+                        if (has_a) {
+                            sm1 = sa;
+                            sm1i = a;
+                        }
+                        bool best_moved = false;
+                        for (int c = c_lo; c < c_hi; ++c) {
+                            if (c == a) continue;
+                            const float pb = wl == v ? lr : __fsub_rd(lr, __fsub_ru(dcv[c], __ldg(dcw + c)));
+                            if (pb >= bd_up) {  // point filter: cannot beat the running best
+                                pm1 = fminf(pm1, pb);
+                                continue;
+                            }
+                            const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
+                            c_dist += 1;
+                            if (s < s_best || (s == s_best && c < best)) {
+                                s_sec = fminf(s_sec, s_best);
+                                s_best = s;
+                                best = c;
+                                best_moved = true;
+                                bd_up = fminf(bd_up, dist_up(s, p));
+                            } else {
+                                s_sec = fminf(s_sec, s);
+                            }
+                            if (s < sm1) {
+                                sm2 = sm1;
+                                sm1 = s;
+                                sm1i = c;
+                            } else {
+                                sm2 = fminf(sm2, s);
+                            }
+                        }
+                        here = best_moved || (has_a && best == a);
+                        val_leave = fminf(pm1, dist_dn(sm1, p));
+                        val = (here && sm1i == best) ? fminf(pm1, dist_dn(sm2, p)) : val_leave;
+                    }
+                    if (here) {
+                        if (bg >= 0 && bg != g) {
+                            // the best left group bg: its bound takes the value with the old best
+                            lbrow[bg] = bg_m1;
+                            lmin = fminf(lmin, bg_m1);
+                        }
+                        bg = g;
+                        bg_val = val;
+                        bg_m1 = val_leave;
+                    } else {
+                        lmin = fminf(lmin, val);
+                    }
+                    lbrow[g] = val;
+                }
+                float lbg_new = bg >= 0 ? fminf(lmin, bg_val) : lmin;
+
+                if (s_sec != INFINITY && unresolved(s_best, s_sec, p)) {
+                    best = settle_full<DP>(p, Cs, gs, n, &s_best, &lbg_new);
+                    c_dist += 3 * (unsigned long long)K;
+                    c_recheck += 1;
+                }
+                p.lbg[n] = lbg_new;
+                p.u[n] = dist_up(s_best, p);
+                p.label[n] = best;
+                p.stamp[n] = make_stamp(v, v);
+                moved = best != a;
+            }
+        }
+        // moved points: one atomic per warp for the list slots
+        const unsigned mm = __ballot_sync(0xffffffffu, moved);
+        if (mm) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ctrl->moved_count, __popc(mm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (moved) {
+                const int slot = base + __popc(mm & ((1u << lane) - 1u));
+                p.moved[slot] = (int32_t)n;
+                p.moved_old[slot] = a;
+            }
+            c_changed += moved ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c_scanned += __shfl_xor_sync(0xffffffffu, c_scanned, o);
+        c_dist += __shfl_xor_sync(0xffffffffu, c_dist, o);
+        c_recheck += __shfl_xor_sync(0xffffffffu, c_recheck, o);
+        c_changed += __shfl_xor_sync(0xffffffffu, c_changed, o);
+    }
+    if (lane == 0) {
+        if (c_scanned) atomicAdd(&ctrl->n_scanned, c_scanned);
+        if (c_dist) atomicAdd(&ctrl->n_dist, c_dist);
+        if (c_recheck) atomicAdd(&ctrl->n_recheck, c_recheck);
+        if (c_changed) atomicAdd(&ctrl->n_changed, c_changed);
+    }
+}
+
+template <int DP>
+cudaError_t launch_tp(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit) {
+    const size_t tail = (size_t)p.K * 4 + (size_t)p.Gp * 4 + (size_t)(p.G + 1) * 4;
+    const size_t cbytes = (size_t)p.K * p.Dp * 4;
+    const bool stage = cbytes + tail <= smem_limit && cbytes < (1u << 31);
+    const size_t smem = (stage ? cbytes : 0) + tail;
+    if (smem > smem_limit) return cudaErrorInvalidConfiguration;
+    auto kern = stage ? k_survivor_tp<DP, true> : k_survivor_tp<DP, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTpThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = ((int64_t)p.N + kTpThreads - 1) / kTpThreads;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms * std::max(per_sm, 1)));
+    count_launch();
+    kern<<<(unsigned)grid, kTpThreads, smem, s>>>(p, respect_done);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool survivor_tp_eligible(const Params &p) {
+    const int dp = dense_dp(p.D);
+    return dp > 0 && dp <= 64 && p.K < 0x7fffffff;
+}
+
+cudaError_t launch_survivor_tp(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit) {
+    smem_limit -= 64;  // static shared (mbarrier)
+    switch (dense_dp(p.D)) {
+    case 4: return launch_tp<4>(p, s, respect_done, num_sms, smem_limit);
+    case 8: return launch_tp<8>(p, s, respect_done, num_sms, smem_limit);
+    case 16: return launch_tp<16>(p, s, respect_done, num_sms, smem_limit);
+    case 32: return launch_tp<32>(p, s, respect_done, num_sms, smem_limit);
+    case 64: return launch_tp<64>(p, s, respect_done, num_sms, smem_limit);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace kp
