@@ -422,6 +422,13 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         INIT_CUDA(dalloc(c, &p.stamp, (size_t)N));
         INIT_CUDA(dalloc(c, &p.lb, (size_t)N * p.Gp));
         INIT_CUDA(dalloc(c, &p.queue, (size_t)N));
+        // survivor queue buckets: labels >> bshift, at most 4096 buckets
+        p.bshift = 0;
+        while (((K - 1) >> p.bshift) >= 4096) ++p.bshift;
+        p.nbucket = ((K - 1) >> p.bshift) + 1;
+        INIT_CUDA(dalloc(c, &p.bcount, (size_t)p.nbucket));
+        INIT_CUDA(dalloc(c, &p.bcursor, (size_t)p.nbucket));
+        INIT_CUDA(cudaMemsetAsync(p.bcount, 0, (size_t)p.nbucket * 4, c->stream));
     }
     INIT_CUDA(dalloc(c, &p.C, (size_t)K * p.Dp));
     INIT_CUDA(dalloc(c, &p.S, (size_t)K * D));
@@ -471,10 +478,11 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.eps_hi = f32_up(1.0 + 2.0 * eps);
     p.eps_lo = f32_dn(1.0 - eps);
     p.tiny = std::ldexp((float)(D + 4), -149);
-    p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : 0.08f;
-
     c->use_tc = o.dense == KM_DENSE_AUTO && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
                 dense_tc_eligible(p, c->smem_optin);
+    // default switch: a tensor-core pair costs about a quarter of a survivor
+    // pair, an FP32 dense pair about half of one
+    p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.25f : 0.5f);
     if (c->use_tc) {  // the two bfloat16 halves of X, made once
         uint16_t *xh, *xl;
         INIT_CUDA(dalloc(c, &xh, (size_t)N * D));
@@ -648,6 +656,7 @@ KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
     KP_CUDA(c, cudaMemsetAsync(p.Dm, 0, (size_t)c->tcap * 4, s));
     KP_CUDA(c, cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
     KP_CUDA(c, cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * kStatsCap, s));
+    if (p.bcount) KP_CUDA(c, cudaMemsetAsync(p.bcount, 0, (size_t)p.nbucket * 4, s));
     KP_CUDA(c, cudaStreamSynchronize(s));
     memset(c->ctrl_host, 0, sizeof(Ctrl));
     c->t_host = 0;

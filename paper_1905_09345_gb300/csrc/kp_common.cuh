@@ -87,7 +87,10 @@ struct Params {
     const int32_t *grp;  // K: group of each centroid
     const int32_t *gstart;  // G + 1: centroids of group g are [gstart[g], gstart[g+1])
 
-    int32_t *queue;      // N: survivors of the global filter
+    int32_t *queue;      // N: survivors of the global filter, grouped by label bucket
+    int32_t *bcount;     // nbucket: survivors per label bucket (label >> bshift)
+    int32_t *bcursor;    // nbucket: next free queue slot of each bucket
+    int32_t nbucket, bshift;
     int32_t *moved;      // N: points whose label changed (dense path)
     int32_t *moved_old;  // N: their previous label (-1: none)
     float *delta;        // K: drift of the last update

@@ -164,22 +164,6 @@ __device__ __forceinline__ float row_norm2(const uint8_t *Ah, const uint8_t *Al,
     return a0 + a1;
 }
 
-// FP32 direct-difference squared distance from global memory (rare path)
-__device__ __forceinline__ float sqdist_global(const float *x, const float *c, int D) {
-    float a0 = 0.f, a1 = 0.f;
-    int i = 0;
-    for (; i + 1 < D; i += 2) {
-        const float t0 = x[i] - c[i], t1 = x[i + 1] - c[i + 1];
-        a0 = fmaf(t0, t0, a0);
-        a1 = fmaf(t1, t1, a1);
-    }
-    if (i < D) {
-        const float t0 = x[i] - c[i];
-        a0 = fmaf(t0, t0, a0);
-    }
-    return a0 + a1;
-}
-
 // FP32 direct-difference squared distance, x in registers (D/4 float4),
 // c a 16-byte-aligned row in global memory
 template <int D>
@@ -200,6 +184,25 @@ __device__ __forceinline__ float sqdist_reg4(const float4 (&x)[D / 4], const flo
         t = x[q + 1].w - c1.w; a1 = fmaf(t, t, a1);
     }
     return a0 + a1;
+}
+
+// FP64 squared distance with the summation order of the FP64 definition
+// (coordinates ascending, no fused multiply-add), x from registers
+template <int D>
+__device__ __forceinline__ double dist2_f64_reg4(const float4 (&x)[D / 4], const float *c) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < D / 4; ++q) {
+        const float4 c4 = __ldg(reinterpret_cast<const float4 *>(c) + q);
+        const float xv[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double t = __dsub_rn((double)xv[j], (double)cv[j]);
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+    }
+    return s;
 }
 
 // Stage the closing group's minimum and return the next boundary (a value
@@ -490,16 +493,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     best = bi;
                     s_exact = bs;
                     if (sec != INFINITY && unresolved(bs, sec, p)) {
+                        // FP64 among the same candidates: every column outside the
+                        // window is strictly farther than the tensor-core winner
                         double bd = INFINITY;
                         int bj = bi;
-                        for (int col = 0; col < K; ++col) {
-                            const float sx = sqdist_global(xg, p.C + (size_t)col * p.Dp, D);
+                        for (int k = 0; k < m; ++k) {
+                            const int col = nc > 4 ? k : (int)((pack >> (8 * (nc - 1 - k))) & 0xffu);
+                            const float *cr = p.C + (size_t)col * p.Dp;
+                            const float sx = sqdist_reg4<D>(xr, cr);
                             if (!unresolved(bs, sx, p)) continue;
-                            const double d64 = dist2_f64(xg, p.C + (size_t)col * p.Dp, D);
-                            if (d64 < bd) { bd = d64; bj = col; }
+                            const double d64 = dist2_f64_reg4<D>(xr, cr);
+                            if (d64 < bd || (d64 == bd && col < bj)) {
+                                bd = d64;
+                                bj = col;
+                            }
                         }
                         best = bj;
-                        s_exact = sqdist_global(xg, p.C + (size_t)bj * p.Dp, D);
+                        s_exact = sqdist_reg4<D>(xr, p.C + (size_t)bj * p.Dp);
                         c_recheck += 1;
                     }
                 }

@@ -7,8 +7,10 @@
 //   k_filter    all N points, one thread per 4 points, coalesced 16-byte
 //               loads of label/u/lbg/stamp: applies the drift since each
 //               point's stamp (bound update) and the global test
-//               u <= lbg; points that fail go to a work queue through a warp
-//               ballot + prefix scan and one atomic per warp (compaction).
+//               u <= lbg, and counts the points that fail per label bucket;
+//   k_filter_scatter  repeats the test and writes the survivors to a work
+//               queue grouped by label (a counting sort: shared-memory
+//               counts per tile, one global atomic per bucket and tile).
 //   k_survivor  one warp per queued point, centroids staged in shared memory
 //               by TMA bulk copies: tightens u to the exact distance and
 //               retests; then the group-level filter (lanes over groups, one
@@ -29,80 +31,176 @@ namespace kp {
 // ---------------------------------------------------------------------------
 constexpr int kFilterThreads = 256;
 
+// The global test of up to four consecutive points: bit j of the result is
+// set when point n0 + j fails it (a survivor); a[] receives the labels.
+__device__ __forceinline__ unsigned global_test4(const Params &p, int v, int64_t n0, int (&a)[4]) {
+    float u[4], lg[4];
+    uint32_t st[4];
+    if (n0 + 3 < p.N) {
+        int4 a4 = *reinterpret_cast<const int4 *>(p.label + n0);
+        float4 u4 = *reinterpret_cast<const float4 *>(p.u + n0);
+        float4 l4 = *reinterpret_cast<const float4 *>(p.lbg + n0);
+        uint4 s4 = *reinterpret_cast<const uint4 *>(p.stamp + n0);
+        a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
+        u[0] = u4.x; u[1] = u4.y; u[2] = u4.z; u[3] = u4.w;
+        lg[0] = l4.x; lg[1] = l4.y; lg[2] = l4.z; lg[3] = l4.w;
+        st[0] = s4.x; st[1] = s4.y; st[2] = s4.z; st[3] = s4.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (n0 + j < p.N) {
+                a[j] = p.label[n0 + j]; u[j] = p.u[n0 + j];
+                lg[j] = p.lbg[n0 + j]; st[j] = p.stamp[n0 + j];
+            } else {
+                a[j] = 0; u[j] = 0.f; lg[j] = INFINITY; st[j] = make_stamp(v, v);
+            }
+        }
+    }
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        // bound update after drift, then the global filter
+        float ue = __fadd_ru(u[j], drift_c(p, v, (int)stamp_u(st[j]), a[j]));
+        float le = __fsub_rd(lg[j], drift_m(p, v, (int)stamp_l(st[j])));
+        if (!(ue <= le)) m |= 1u << j;
+    }
+    return m;
+}
+
+// Pass 1 of the compaction: counts the survivors per label bucket (label >>
+// bshift) into bcount and their total into queue_count.  The last block to
+// finish decides whether this iteration runs the dense pass and, if not,
+// turns the counts into the start offsets (bcursor) of each bucket's segment
+// of the queue.
 __global__ void __launch_bounds__(kFilterThreads) k_filter(Params p, int respect_done) {
+    extern __shared__ int hist[];  // nbucket counters
+    __shared__ int last;
+    __shared__ unsigned long long blk_total;
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
     const int v = ctrl->v;
     const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < p.nbucket; i += kFilterThreads) hist[i] = 0;
+    if (threadIdx.x == 0) blk_total = 0;
+    __syncthreads();
     const int64_t warp = ((int64_t)blockIdx.x * kFilterThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kFilterThreads) >> 5;
     unsigned long long my_surv = 0;
     // each warp handles 128 consecutive points per step (4 per lane)
     for (int64_t wb = warp * 128; wb < p.N; wb += nwarps * 128) {
-        const int64_t n0 = wb + lane * 4;
         int a[4];
-        float u[4], lg[4];
-        uint32_t st[4];
-        if (n0 + 3 < p.N) {
-            int4 a4 = *reinterpret_cast<const int4 *>(p.label + n0);
-            float4 u4 = *reinterpret_cast<const float4 *>(p.u + n0);
-            float4 l4 = *reinterpret_cast<const float4 *>(p.lbg + n0);
-            uint4 s4 = *reinterpret_cast<const uint4 *>(p.stamp + n0);
-            a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
-            u[0] = u4.x; u[1] = u4.y; u[2] = u4.z; u[3] = u4.w;
-            lg[0] = l4.x; lg[1] = l4.y; lg[2] = l4.z; lg[3] = l4.w;
-            st[0] = s4.x; st[1] = s4.y; st[2] = s4.z; st[3] = s4.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (n0 + j < p.N) {
-                    a[j] = p.label[n0 + j]; u[j] = p.u[n0 + j];
-                    lg[j] = p.lbg[n0 + j]; st[j] = p.stamp[n0 + j];
-                } else {
-                    a[j] = 0; u[j] = 0.f; lg[j] = INFINITY; st[j] = make_stamp(v, v);
-                }
-            }
-        }
-        unsigned m = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            // bound update after drift, then the global filter
-            float ue = __fadd_ru(u[j], drift_c(p, v, (int)stamp_u(st[j]), a[j]));
-            float le = __fsub_rd(lg[j], drift_m(p, v, (int)stamp_l(st[j])));
-            if (!(ue <= le)) m |= 1u << j;
-        }
-        // compaction: warp prefix over per-lane survivor counts
-        int cnt = __popc(m);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        int base = 0;
-        if (lane == 31) base = atomicAdd(&ctrl->queue_count, total);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int pos = base + incl - cnt;
+        const unsigned m = global_test4(p, v, wb + lane * 4, a);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (m & (1u << j)) p.queue[pos++] = (int)(n0 + j);
-        my_surv += (lane == 0) ? (unsigned long long)total : 0ull;
+            if (m & (1u << j)) atomicAdd(&hist[a[j] >> p.bshift], 1);
+        my_surv += __popc(m);
     }
-    if (lane == 0 && my_surv) atomicAdd(&ctrl->n_survivors, my_surv);
-    // the last block to finish decides whether this iteration runs the dense pass
-    __shared__ int last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_surv += __shfl_xor_sync(0xffffffffu, my_surv, o);
+    if (lane == 0 && my_surv) atomicAdd(&blk_total, my_surv);
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.nbucket; i += kFilterThreads)
+        if (hist[i]) atomicAdd(&p.bcount[i], hist[i]);
+    if (threadIdx.x == 0 && blk_total) {
+        atomicAdd(&ctrl->queue_count, (int)blk_total);
+        atomicAdd(&ctrl->n_survivors, blk_total);
+    }
+    // the last block to finish decides dense versus filtered and lays out the queue
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&ctrl->filter_ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const int q = *(volatile int *)&ctrl->queue_count;
-        ctrl->dense_mode = (double)q > (double)p.dense_frac * (double)p.N;
+    if (!last) return;
+    __threadfence();
+    // predicted survivor distance evaluations: the survivors times the
+    // evaluations per survivor of the previous filtered iteration (one group's
+    // worth plus the tightening when there is none); dense when above
+    // dense_frac * N * K
+    const int q = *(volatile int *)&ctrl->queue_count;
+    double per_surv = fmin(1.0 + (double)p.K / (double)p.G, (double)p.K);
+    const int t = ctrl->t;
+    if (t >= 1) {
+        const kmeans_iter_stats &ps = p.stats[(t - 1) % kStatsCap];
+        if (ps.path == KM_PATH_FILTERED && ps.n_survivors > 0)
+            per_surv = (double)ps.n_dist / (double)ps.n_survivors;
+    }
+    const int dense = p.dense_frac < 1.0f &&
+                      (double)q * fmin(per_surv, (double)p.K) > (double)p.dense_frac * (double)p.N * (double)p.K;
+    if (threadIdx.x == 0) {
+        ctrl->dense_mode = dense;
         ctrl->filter_ticket = 0;
+    }
+    if (dense) return;
+    // exclusive scan of the bucket counts: each thread sums a contiguous run
+    const int per = (p.nbucket + kFilterThreads - 1) / kFilterThreads;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, p.nbucket);
+    int run = 0;
+    for (int b = b0; b < b1; ++b) run += __ldcg(p.bcount + b);
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __shared__ int wsum[kFilterThreads / 32];
+    if (lane == 31) wsum[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    int off = incl - run;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) off += wsum[w];
+    for (int b = b0; b < b1; ++b) {
+        p.bcursor[b] = off;
+        off += __ldcg(p.bcount + b);
+    }
+}
+
+// Pass 2: the same global test again (the inputs are unchanged, so the
+// decisions are the same), and each survivor is written to its bucket's
+// segment of the queue: per tile of 1024 points a block counts its survivors
+// per bucket in shared memory, reserves each bucket's range with one global
+// atomic, and places the points.  The queue then holds the survivors grouped
+// by label, so that neighbouring threads of the survivor kernel tend to visit
+// the same groups and centroids.  Also clears bcount for the next iteration.
+__global__ void __launch_bounds__(kFilterThreads) k_filter_scatter(Params p, int respect_done) {
+    extern __shared__ int sh[];  // nbucket counters | nbucket bases
+    int *cnt = sh;
+    int *base = sh + p.nbucket;
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    for (int64_t i = (int64_t)blockIdx.x * kFilterThreads + threadIdx.x; i < p.nbucket;
+         i += (int64_t)gridDim.x * kFilterThreads)
+        p.bcount[i] = 0;
+    if (*(volatile int *)&ctrl->dense_mode) return;
+    const int v = ctrl->v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kTile = kFilterThreads * 4;
+    for (int i = threadIdx.x; i < p.nbucket; i += kFilterThreads) cnt[i] = 0;
+    __syncthreads();
+    for (int64_t t0 = (int64_t)blockIdx.x * kTile; t0 < p.N; t0 += (int64_t)gridDim.x * kTile) {
+        const int64_t n0 = t0 + warp * 128 + lane * 4;
+        int a[4];
+        const unsigned m = n0 < p.N ? global_test4(p, v, n0, a) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (m & (1u << j)) atomicAdd(&cnt[a[j] >> p.bshift], 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < p.nbucket; i += kFilterThreads) {
+            const int c = cnt[i];
+            base[i] = c ? atomicAdd(&p.bcursor[i], c) : 0;
+            cnt[i] = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (m & (1u << j)) {
+                const int b = a[j] >> p.bshift;
+                p.queue[base[b] + atomicAdd(&cnt[b], 1)] = (int32_t)(n0 + j);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < p.nbucket; i += kFilterThreads) cnt[i] = 0;
+        __syncthreads();
     }
 }
 
@@ -406,8 +504,15 @@ cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int
     int64_t warps = (p.N + 127) / 128;
     int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms * 8);
     grid = std::max<int64_t>(grid, 1);
+    const size_t smem1 = (size_t)p.nbucket * 4, smem2 = 2 * smem1;
+    cudaError_t e = cudaFuncSetAttribute(k_filter_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
     count_launch();
-    k_filter<<<(unsigned)grid, kFilterThreads, 0, s>>>(p, respect_done);
+    k_filter<<<(unsigned)grid, kFilterThreads, smem1, s>>>(p, respect_done);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_filter_scatter<<<(unsigned)grid, kFilterThreads, smem2, s>>>(p, respect_done);
     return cudaGetLastError();
 }
 

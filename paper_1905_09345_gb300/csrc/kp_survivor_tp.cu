@@ -103,25 +103,18 @@ __device__ __forceinline__ double dist2_f64_xr(const float4 (&xr)[DP / 4], const
     return s;
 }
 
-// Rare path: the FP32 results do not separate the best from the runner-up.
-// Scan all K centroids in FP32, settle the unresolved ones in FP64 (lowest
-// index on equal FP64 distances), then rebuild every group bound from the
-// full scan.  Returns the winner; *s_win is its FP32 squared distance.
+// Rare path: the FP32 results do not separate the best (FP32 value s1, index
+// i1) from the runner-up.  Every centroid whose FP32 distance the error bound
+// cannot separate from s1 is settled in FP64 (lowest index on equal FP64
+// distances).  When the FP64 winner is not i1, every group bound is rebuilt
+// from a full FP32 scan (the bounds written by the filtered scan assumed i1).
+// Returns the winner; *s_win is its FP32 squared distance.
 template <int DP>
-__device__ __noinline__ int settle_full(const Params &p, const float *Cs, const int32_t *gs, int64_t n,
-                                        float *s_win, float *lbg_out) {
+__device__ __noinline__ int settle_full(const Params &p, const float *Cs, const int32_t *gs, int64_t n, float s1,
+                                        int i1, float *s_win, float *lbg_out) {
     const int K = p.K, G = p.G, D = p.D;
     float4 xr[DP / 4];
     load_x<DP>(p, n, xr);
-    float s1 = INFINITY;
-    int i1 = 0;
-    for (int c = 0; c < K; ++c) {
-        const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
-        if (s < s1) {
-            s1 = s;
-            i1 = c;
-        }
-    }
     double bd = INFINITY;
     int bi = i1;
     for (int c = 0; c < K; ++c) {
@@ -132,6 +125,10 @@ __device__ __noinline__ int settle_full(const Params &p, const float *Cs, const 
             bd = d;
             bi = c;
         }
+    }
+    if (bi == i1) {
+        *s_win = s1;
+        return bi;
     }
     float lmin = INFINITY;
     float *lbrow = p.lb + n * p.Gp;
@@ -294,8 +291,8 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
                 float lbg_new = bg >= 0 ? fminf(lmin, bg_val) : lmin;
 
                 if (s_sec != INFINITY && unresolved(s_best, s_sec, p)) {
-                    best = settle_full<DP>(p, Cs, gs, n, &s_best, &lbg_new);
-                    c_dist += 3 * (unsigned long long)K;
+                    best = settle_full<DP>(p, Cs, gs, n, s_best, best, &s_best, &lbg_new);
+                    c_dist += (unsigned long long)K;
                     c_recheck += 1;
                 }
                 p.lbg[n] = lbg_new;
