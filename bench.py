@@ -197,7 +197,9 @@ def algorithmic(kind: str, w, stats: list, launches: int) -> tuple[str, float, s
     Gp = (G + 3) // 4 * 4
     filt = [s for s in stats if s["iter"] > 0]
     if kind == "dense_assign":
-        return "alu", 3.0 * N * K * D, "flop"
+        # X read once (FP32, or its two bfloat16 halves: 4 bytes per coordinate
+        # either way) and label/u/lbg/stamp plus the lb row written per point
+        return "hbm", N * (4.0 * D + 16.0 + 4.0 * Gp), "byte"
     if kind == "filter":
         surv = sum(s["n_survivors"] for s in filt) / max(1, len(filt))
         return "hbm", 16.0 * N + 4.0 * surv, "byte"
@@ -221,10 +223,10 @@ def source_sha(files) -> str:
 
 
 KERNEL_SOURCES = {
-    "dense_assign": ["paper_1905_09345_gb300/csrc/kp_dense.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "dense_assign": ["paper_1905_09345_gb300/csrc/kp_dense_tc.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "apply_moves": ["paper_1905_09345_gb300/csrc/kp_dense.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "filter": ["paper_1905_09345_gb300/csrc/kp_filter.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
-    "survivor": ["paper_1905_09345_gb300/csrc/kp_filter.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "survivor": ["paper_1905_09345_gb300/csrc/kp_survivor_tp.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "update": ["paper_1905_09345_gb300/csrc/kp_update.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
 }
 
@@ -333,7 +335,7 @@ def run_ours(args):
 
     # --- plain GPU Lloyd on the same GPU and inputs: tensor cores, FP32 ---
     lloyd = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream)
-    lt, li, _, _ = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd (TF32 tensor cores)")
+    lt, li, _, _ = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd (BF16x3 tensor cores)")
     lloyd_value = w.N * statistics.mean(li) / (statistics.mean(lt) / 1e3)
     lloyd.close()
     lloyd32 = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream, dense=kpynq.KM_DENSE_FP32)
@@ -420,7 +422,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "skip_fraction": skip,
         "plain_lloyd": {"value": lloyd_value, "ms_per_step": statistics.mean(lt), "iters": statistics.mean(li),
-                        "dense": "TF32 tensor cores + exact settle"},
+                        "dense": "BF16x3 tensor cores (tcgen05) + exact FP32/FP64 settle"},
         "vs_plain_lloyd": value / lloyd_value,
         "plain_lloyd_fp32": {"value": lloyd32_value, "ms_per_step": statistics.mean(lt32),
                              "iters": statistics.mean(li32), "dense": "FP32 CUDA cores"},

@@ -90,13 +90,11 @@ typedef struct {
                             graph); see kmeans_get_profile */
     void *stream;        /* cudaStream_t; NULL = legacy default stream */
     int32_t dense;       /* KM_DENSE_*: engine of the dense (all-pairs) passes */
-    float dense_switch;  /* a filtered iteration runs the dense pass instead when
-                            its predicted distance evaluations (survivors of the
-                            global filter times the evaluations per survivor of
-                            the previous filtered iteration; 1 + K/G when there
-                            is none) exceed this fraction of N*K; 0 = library
-                            default (0.25 with the tensor-core engine, 0.5
-                            without), >= 1 = never */
+    float dense_switch;  /* a filtered iteration whose global filter leaves more
+                            than this fraction of the points runs the dense pass
+                            instead (which also makes every bound exact again);
+                            0 = library default (0.7 with the tensor-core
+                            engine, 0.9 without), >= 1 = never */
     int64_t reserved[5]; /* must be zero */
 } kmeans_options;
 

@@ -237,6 +237,10 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
                              : launch_dense_assign(p, s, first, respect_done, n);
         });
         if (e != cudaSuccess) return e;
+        if (c->use_tc) {
+            e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_settle(p, s, first, respect_done, n); });
+            if (e != cudaSuccess) return e;
+        }
         return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, first ? 1 : 0, respect_done, n); });
     }
     // filtered: global filter, then either the survivor kernel or -- when the
@@ -251,6 +255,10 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
                          : launch_dense_assign(p, s, 0, respect_done, n, 1);
     });
     if (e != cudaSuccess) return e;
+    if (c->use_tc) {  // no rows queued unless the dense pass ran
+        e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_settle(p, s, 0, respect_done, n); });
+        if (e != cudaSuccess) return e;
+    }
     // both the survivor kernel and the dense pass append to the moved-point list
     return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, 0, respect_done, n); });
 }
@@ -480,9 +488,9 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.tiny = std::ldexp((float)(D + 4), -149);
     c->use_tc = o.dense == KM_DENSE_AUTO && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
                 dense_tc_eligible(p, c->smem_optin);
-    // default switch: a tensor-core pair costs about a quarter of a survivor
-    // pair, an FP32 dense pair about half of one
-    p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.25f : 0.5f);
+    // default switch: the tensor-core dense pass costs about as much as the
+    // survivor kernel with 70% of the points surviving; the FP32 one more
+    p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.7f : 0.9f);
     if (c->use_tc) {  // the two bfloat16 halves of X, made once
         uint16_t *xh, *xl;
         INIT_CUDA(dalloc(c, &xh, (size_t)N * D));
@@ -490,6 +498,9 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         INIT_CUDA(launch_split_x(p.X, N, D, xh, xl, s, c->num_sms));
         p.Xh = xh;
         p.Xl = xl;
+        SettleReq *sq;
+        INIT_CUDA(dalloc(c, &sq, (size_t)N));
+        p.sreq = sq;
     }
 
     if (o.validate) {

@@ -51,12 +51,25 @@ struct Ctrl {
     int32_t dense_mode;   // the current filtered iteration runs the dense pass
     uint32_t filter_ticket;  // last-block-done counter of the filter kernel
     unsigned long long kernels;  // kernels of this context run on the device
+    int32_t settle_count;  // rows queued for the exact settle by the tensor-core pass
 };
 
 // every kernel of a context counts itself once (block 0, thread 0)
 __device__ __forceinline__ void count_kernel(Ctrl *c) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->kernels, 1ull);
 }
+
+// A row the tensor-core pass could not decide: its runner-up lies inside the
+// error window of the winner.
+struct SettleReq {
+    int32_t n;       // point
+    int32_t old;     // label before this pass (-1: none)
+    int32_t i1;      // tensor-core winner (the bounds were written for it)
+    int32_t nc;      // window columns found (> 4: overflow, all K are candidates)
+    uint32_t pack;   // up to four window columns, 8 bits each, first found highest
+    float lb_alt;    // group bound that holds for every column (from the smallest estimate)
+    int32_t pad0, pad1;
+};
 
 // Everything a kernel needs, passed by value.
 struct Params {
@@ -91,6 +104,7 @@ struct Params {
     int32_t *bcount;     // nbucket: survivors per label bucket (label >> bshift)
     int32_t *bcursor;    // nbucket: next free queue slot of each bucket
     int32_t nbucket, bshift;
+    struct SettleReq *sreq;  // N: rows the tensor-core pass left to the exact settle
     int32_t *moved;      // N: points whose label changed (dense path)
     int32_t *moved_old;  // N: their previous label (-1: none)
     float *delta;        // K: drift of the last update
@@ -272,6 +286,7 @@ cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint1
                            int num_sms);
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);
+cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);
 cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms,
                                int if_dense = 0);
 cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms);

@@ -164,47 +164,6 @@ __device__ __forceinline__ float row_norm2(const uint8_t *Ah, const uint8_t *Al,
     return a0 + a1;
 }
 
-// FP32 direct-difference squared distance, x in registers (D/4 float4),
-// c a 16-byte-aligned row in global memory
-template <int D>
-__device__ __forceinline__ float sqdist_reg4(const float4 (&x)[D / 4], const float *c) {
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < D / 4; q += 2) {
-        const float4 c0 = __ldg(reinterpret_cast<const float4 *>(c) + q);
-        const float4 c1 = __ldg(reinterpret_cast<const float4 *>(c) + q + 1);
-        float t;
-        t = x[q].x - c0.x; a0 = fmaf(t, t, a0);
-        t = x[q].y - c0.y; a0 = fmaf(t, t, a0);
-        t = x[q].z - c0.z; a0 = fmaf(t, t, a0);
-        t = x[q].w - c0.w; a0 = fmaf(t, t, a0);
-        t = x[q + 1].x - c1.x; a1 = fmaf(t, t, a1);
-        t = x[q + 1].y - c1.y; a1 = fmaf(t, t, a1);
-        t = x[q + 1].z - c1.z; a1 = fmaf(t, t, a1);
-        t = x[q + 1].w - c1.w; a1 = fmaf(t, t, a1);
-    }
-    return a0 + a1;
-}
-
-// FP64 squared distance with the summation order of the FP64 definition
-// (coordinates ascending, no fused multiply-add), x from registers
-template <int D>
-__device__ __forceinline__ double dist2_f64_reg4(const float4 (&x)[D / 4], const float *c) {
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < D / 4; ++q) {
-        const float4 c4 = __ldg(reinterpret_cast<const float4 *>(c) + q);
-        const float xv[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
-        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const double t = __dsub_rn((double)xv[j], (double)cv[j]);
-            s = __dadd_rn(s, __dmul_rn(t, t));
-        }
-    }
-    return s;
-}
-
 // Stage the closing group's minimum and return the next boundary (a value
 // no column index reaches once the last group is open).
 __device__ __noinline__ int close_group(float *row, const int *gs, int &g, float gm1, int K) {
@@ -450,12 +409,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             row[cur_g] = gm1;
             const float thr = __fadd_ru(b1, twoE);
 
-            // settle exactly where the runner-up is inside the error window: a
-            // rescan of the accumulators collects the window's columns (up to
-            // four ids packed in one register), then they are evaluated exactly,
-            // lane-parallel, from global memory
-            int best = i1;
-            float s_exact = -1.f;
+            // Rows whose runner-up is inside the error window are settled
+            // exactly by k_settle afterwards: a rescan of the accumulators
+            // collects the window's columns (up to four ids packed in one
+            // register; more is an overflow that k_settle answers with all K),
+            // and the row goes to the settle queue.  The epilogue writes such a
+            // row's bounds as if the tensor-core winner i1 won; k_settle
+            // corrects them when it does not.
+            const int old = valid ? (first ? -1 : p.label[n]) : -1;
             const bool need = valid && b2 <= thr;
             if (__any_sync(0xffffffffu, need)) {
                 uint32_t pack = 0;
@@ -471,47 +432,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         nc += in;
                     }
                 }
+                const unsigned nm = __ballot_sync(0xffffffffu, need);
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&ctrl->settle_count, __popc(nm));
+                base = __shfl_sync(0xffffffffu, base, 0);
                 if (need) {
-                    const float *xg = p.X + n * D;
-                    float4 xr[D / 4];
-#pragma unroll
-                    for (int q4 = 0; q4 < D / 4; ++q4) xr[q4] = __ldg(reinterpret_cast<const float4 *>(xg) + q4);
-                    float bs = INFINITY, sec = INFINITY;
-                    int bi = i1;
-                    const int m = nc > 4 ? K : nc;  // overflow (rare): every centroid
-                    for (int k = 0; k < m; ++k) {
-                        const int col = nc > 4 ? k : (int)((pack >> (8 * (nc - 1 - k))) & 0xffu);
-                        const float sx = sqdist_reg4<D>(xr, p.C + (size_t)col * p.Dp);
-                        if (sx < bs || (sx == bs && col < bi)) {
-                            sec = bs;
-                            bs = sx;
-                            bi = col;
-                        } else if (sx < sec) {
-                            sec = sx;
-                        }
-                    }
-                    best = bi;
-                    s_exact = bs;
-                    if (sec != INFINITY && unresolved(bs, sec, p)) {
-                        // FP64 among the same candidates: every column outside the
-                        // window is strictly farther than the tensor-core winner
-                        double bd = INFINITY;
-                        int bj = bi;
-                        for (int k = 0; k < m; ++k) {
-                            const int col = nc > 4 ? k : (int)((pack >> (8 * (nc - 1 - k))) & 0xffu);
-                            const float *cr = p.C + (size_t)col * p.Dp;
-                            const float sx = sqdist_reg4<D>(xr, cr);
-                            if (!unresolved(bs, sx, p)) continue;
-                            const double d64 = dist2_f64_reg4<D>(xr, cr);
-                            if (d64 < bd || (d64 == bd && col < bj)) {
-                                bd = d64;
-                                bj = col;
-                            }
-                        }
-                        best = bj;
-                        s_exact = sqdist_reg4<D>(xr, p.C + (size_t)bj * p.Dp);
-                        c_recheck += 1;
-                    }
+                    SettleReq q;
+                    q.n = (int32_t)n;
+                    q.old = old;
+                    q.i1 = i1;
+                    q.nc = nc;
+                    q.pack = pack;
+                    // every column is at least b1: when i1 loses, this bounds both
+                    // i1's group (which now keeps i1) and the winner's group
+                    q.lb_alt = sqrt_dn(__fsub_rd(__fadd_rd(xlo, b1), E));
+                    q.pad0 = q.pad1 = 0;
+                    p.sreq[base + __popc(nm & ((1u << lane) - 1u))] = q;
                 }
             }
             // accumulators no longer needed
@@ -519,10 +455,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             __syncwarp();
             if (lane == 0) bar_arrive(&acc_empty[grp_id]);
 
+            const int best = i1;
             if (valid) {
                 c_dist += (unsigned long long)K;
-                const int old = first ? -1 : p.label[n];
-                p.label[n] = best;
+                if (!need) p.label[n] = best;
                 if (bounds) {
                     // s_c >= xn_lo + t_c - E for every column c
                     for (int g = 0; g < G; ++g) {
@@ -537,10 +473,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     float mm = INFINITY;
                     for (int g = 0; g < G; ++g) mm = fminf(mm, row[g]);
                     p.lbg[n] = mm;
-                    p.u[n] = s_exact >= 0.f ? dist_up(s_exact, p) : sqrt_up(__fadd_ru(__fadd_ru(xup, b1), E));
+                    p.u[n] = sqrt_up(__fadd_ru(__fadd_ru(xup, b1), E));
                     p.stamp[n] = make_stamp(v, v);
                 }
-                if (old != best) {
+                if (!need && old != best) {
                     c_changed += 1;
                     if (!first) {
                         const int slot = atomicAdd(&ctrl->moved_count, 1);
@@ -582,6 +518,106 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cfg.tmem_cols)
                      : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_settle: the exact decision for the rows the tensor-core epilogue queued
+// (runner-up inside the error window).  One warp per row, lanes over the
+// coordinates: FP32 direct-difference distances of the window's candidates
+// (in ascending index order; every other centroid is strictly farther than
+// the tensor-core winner), FP64 with the summation order of the FP64
+// definition where FP32 cannot separate them.  Writes the label, corrects
+// u / lb / lbg when the winner is not i1, and appends label changes to the
+// moved-point list.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) k_settle(Params p, int first, int respect_done) {
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    const int count = *(volatile int *)&ctrl->settle_count;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool bounds = p.algo == KM_ALGO_FILTERED;
+    constexpr int kPer = D / 32;
+    unsigned long long c_changed = 0, c_recheck = 0;
+    for (int64_t it = warp; it < count; it += nwarps) {
+        const SettleReq q = p.sreq[it];
+        const int64_t n = q.n;
+        float xv[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) xv[j] = __ldg(p.X + n * D + lane + 32 * j);
+        const int m = q.nc > 4 ? p.K : q.nc;  // overflow: every centroid
+        auto cand = [&](int k) { return q.nc > 4 ? k : (int)((q.pack >> (8 * (q.nc - 1 - k))) & 0xffu); };
+        auto fp32 = [&](int col) {
+            const float *c = p.C + (size_t)col * p.Dp;
+            float a = 0.f;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const float t = xv[j] - __ldg(c + lane + 32 * j);
+                a = fmaf(t, t, a);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            return a;
+        };
+        float bs = INFINITY, sec = INFINITY;
+        int bi = q.i1;
+        for (int k = 0; k < m; ++k) {
+            const int col = cand(k);
+            const float sx = fp32(col);
+            if (sx < bs || (sx == bs && col < bi)) {
+                sec = bs;
+                bs = sx;
+                bi = col;
+            } else if (sx < sec) {
+                sec = sx;
+            }
+        }
+        if (sec != INFINITY && unresolved(bs, sec, p)) {
+            double bd = INFINITY;
+            int bj = bi;
+            for (int k = 0; k < m; ++k) {
+                const int col = cand(k);
+                if (!unresolved(bs, fp32(col), p)) continue;
+                if (lane == 0) {
+                    const double d64 = dist2_f64(p.X + n * D, p.C + (size_t)col * p.Dp, D);
+                    if (d64 < bd || (d64 == bd && col < bj)) {
+                        bd = d64;
+                        bj = col;
+                    }
+                }
+            }
+            bj = __shfl_sync(0xffffffffu, bj, 0);
+            if (bj != bi) bs = fp32(bj);
+            bi = bj;
+            c_recheck += 1;
+        }
+        if (lane == 0) {
+            p.label[n] = bi;
+            if (bounds) {
+                p.u[n] = dist_up(bs, p);
+                if (bi != q.i1) {
+                    p.lb[n * p.Gp + p.grp[q.i1]] = q.lb_alt;
+                    p.lb[n * p.Gp + p.grp[bi]] = q.lb_alt;
+                    p.lbg[n] = q.lb_alt;
+                }
+            }
+            if (bi != q.old) {
+                c_changed += 1;
+                if (!first) {
+                    const int slot = atomicAdd(&ctrl->moved_count, 1);
+                    p.moved[slot] = (int32_t)n;
+                    p.moved_old[slot] = q.old;
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        if (c_changed) atomicAdd(&ctrl->n_changed, c_changed);
+        if (c_recheck) atomicAdd(&ctrl->n_recheck, c_recheck);
     }
 }
 
@@ -692,6 +728,15 @@ cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_don
 }
 
 }  // namespace
+
+cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms) {
+    count_launch();
+    const unsigned grid = (unsigned)num_sms * 8;
+    if (p.D == 64) k_settle<64><<<grid, 256, 0, s>>>(p, first, respect_done);
+    else if (p.D == 128) k_settle<128><<<grid, 256, 0, s>>>(p, first, respect_done);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 bool dense_tc_eligible(const Params &p, size_t smem_limit) {
     TcCfg cfg;

@@ -113,20 +113,12 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(Params p, int respect
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // predicted survivor distance evaluations: the survivors times the
-    // evaluations per survivor of the previous filtered iteration (one group's
-    // worth plus the tightening when there is none); dense when above
-    // dense_frac * N * K
+    // dense when the survivors exceed dense_frac * N: the survivor kernel's
+    // cost grows with the survivors, the dense pass costs the same for any
+    // and leaves every bound exact (tight bounds make the next iterations'
+    // global filter effective again)
     const int q = *(volatile int *)&ctrl->queue_count;
-    double per_surv = fmin(1.0 + (double)p.K / (double)p.G, (double)p.K);
-    const int t = ctrl->t;
-    if (t >= 1) {
-        const kmeans_iter_stats &ps = p.stats[(t - 1) % kStatsCap];
-        if (ps.path == KM_PATH_FILTERED && ps.n_survivors > 0)
-            per_surv = (double)ps.n_dist / (double)ps.n_survivors;
-    }
-    const int dense = p.dense_frac < 1.0f &&
-                      (double)q * fmin(per_surv, (double)p.K) > (double)p.dense_frac * (double)p.N * (double)p.K;
+    const int dense = p.dense_frac < 1.0f && (double)q > (double)p.dense_frac * (double)p.N;
     if (threadIdx.x == 0) {
         ctrl->dense_mode = dense;
         ctrl->filter_ticket = 0;

@@ -33,15 +33,19 @@ namespace {
 
 constexpr int kTpThreads = 256;
 
-// packed pair of FP32 values (one 64-bit register pair)
+// x is kept as packed pairs of FP32 values: xr[q] holds coordinates
+// 4q .. 4q+3 as two 64-bit registers (low half = lower coordinate)
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
     return r;
 }
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 __device__ __forceinline__ float hsum2(unsigned long long v) {
     float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    unpack2(v, lo, hi);
     return lo + hi;
 }
 
@@ -49,16 +53,16 @@ __device__ __forceinline__ float hsum2(unsigned long long v) {
 // subtract and fused multiply-add (each lane of a pair is an ordinary
 // round-to-nearest FP32 operation): four partial sums of D/4 terms each, so
 // the FP32 error bound of a D-term sum covers it.  Padding coordinates are
-// zero on both sides.
+// zero on both sides; c is a 16-byte-aligned row.
 template <int DP>
-__device__ __forceinline__ float sqdist_xr(const float4 (&xr)[DP / 4], const float *__restrict__ c) {
+__device__ __forceinline__ float sqdist_xr(const ulonglong2 (&xr)[DP / 4], const float *__restrict__ c) {
     unsigned long long a0 = 0ull, a1 = 0ull;
 #pragma unroll
     for (int q = 0; q < DP / 4; ++q) {
-        const float4 c4 = *reinterpret_cast<const float4 *>(c + 4 * q);
+        const ulonglong2 c2 = *reinterpret_cast<const ulonglong2 *>(c + 4 * q);
         unsigned long long d0, d1;
-        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(pack2(xr[q].x, xr[q].y)), "l"(pack2(c4.x, c4.y)));
-        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(pack2(xr[q].z, xr[q].w)), "l"(pack2(c4.z, c4.w)));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(xr[q].x), "l"(c2.x));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(xr[q].y), "l"(c2.y));
         asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
         asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
     }
@@ -66,20 +70,21 @@ __device__ __forceinline__ float sqdist_xr(const float4 (&xr)[DP / 4], const flo
 }
 
 template <int DP>
-__device__ __forceinline__ void load_x(const Params &p, int64_t n, float4 (&xr)[DP / 4]) {
+__device__ __forceinline__ void load_x(const Params &p, int64_t n, ulonglong2 (&xr)[DP / 4]) {
     const int D = p.D;
     const float *xg = p.X + n * D;
     if (p.x_vec4) {
 #pragma unroll
         for (int q = 0; q < DP / 4; ++q)
-            xr[q] = 4 * q < D ? __ldg(reinterpret_cast<const float4 *>(xg) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xr[q] = 4 * q < D ? __ldg(reinterpret_cast<const ulonglong2 *>(xg) + q) : make_ulonglong2(0ull, 0ull);
     } else {
 #pragma unroll
         for (int q = 0; q < DP / 4; ++q) {
-            xr[q].x = 4 * q + 0 < D ? __ldg(xg + 4 * q + 0) : 0.f;
-            xr[q].y = 4 * q + 1 < D ? __ldg(xg + 4 * q + 1) : 0.f;
-            xr[q].z = 4 * q + 2 < D ? __ldg(xg + 4 * q + 2) : 0.f;
-            xr[q].w = 4 * q + 3 < D ? __ldg(xg + 4 * q + 3) : 0.f;
+            const float x0 = 4 * q + 0 < D ? __ldg(xg + 4 * q + 0) : 0.f;
+            const float x1 = 4 * q + 1 < D ? __ldg(xg + 4 * q + 1) : 0.f;
+            const float x2 = 4 * q + 2 < D ? __ldg(xg + 4 * q + 2) : 0.f;
+            const float x3 = 4 * q + 3 < D ? __ldg(xg + 4 * q + 3) : 0.f;
+            xr[q] = make_ulonglong2(pack2(x0, x1), pack2(x2, x3));
         }
     }
 }
@@ -87,11 +92,13 @@ __device__ __forceinline__ void load_x(const Params &p, int64_t n, float4 (&xr)[
 // FP64 squared distance, coordinates ascending, no fused multiply-add (the
 // summation order of the FP64 definition)
 template <int DP>
-__device__ __forceinline__ double dist2_f64_xr(const float4 (&xr)[DP / 4], const float *__restrict__ c, int D) {
+__device__ __forceinline__ double dist2_f64_xr(const ulonglong2 (&xr)[DP / 4], const float *__restrict__ c, int D) {
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < DP / 4; ++q) {
-        const float xv[4] = {xr[q].x, xr[q].y, xr[q].z, xr[q].w};
+        float xv[4];
+        unpack2(xr[q].x, xv[0], xv[1]);
+        unpack2(xr[q].y, xv[2], xv[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (4 * q + j < D) {
@@ -113,7 +120,7 @@ template <int DP>
 __device__ __noinline__ int settle_full(const Params &p, const float *Cs, const int32_t *gs, int64_t n, float s1,
                                         int i1, float *s_win, float *lbg_out) {
     const int K = p.K, G = p.G, D = p.D;
-    float4 xr[DP / 4];
+    ulonglong2 xr[DP / 4];
     load_x<DP>(p, n, xr);
     double bd = INFINITY;
     int bi = i1;
@@ -146,6 +153,20 @@ __device__ __noinline__ int settle_full(const Params &p, const float *Cs, const 
     return bi;
 }
 
+// shared-memory layout (in 4-byte words, each part 16-byte aligned):
+// [C, K x Dp, when staged] | Dc[v] (K) | Dg[v] (Gp) | gstart (G + 1) | grp (K)
+struct TpLayout {
+    size_t dcv, dgv, gs, grp, total;
+    __host__ __device__ static size_t up4(size_t x) { return (x + 3) & ~(size_t)3; }
+    __host__ __device__ TpLayout(const Params &p, bool stage_c) {
+        dcv = stage_c ? (size_t)p.K * p.Dp : 0;
+        dgv = up4(dcv + p.K);
+        gs = up4(dgv + p.Gp);
+        grp = up4(gs + p.G + 1);
+        total = grp + p.K;
+    }
+};
+
 template <int DP, bool STAGE>
 __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int respect_done) {
     extern __shared__ __align__(128) float smem[];
@@ -159,17 +180,17 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
     const int v = ctrl->v;
     const int K = p.K, G = p.G, Gp = p.Gp;
 
-    // shared layout: [C (K x Dp) when staged] Dc[v] (K) | Dg[v] (Gp) | gstart (G + 1)
+    const TpLayout L(p, STAGE);
     const float *Cs = p.C;
-    float *tail = smem;
     if constexpr (STAGE) {
         if (!stage_to_smem(smem, p.C, (uint32_t)((size_t)K * p.Dp * 4), &bar, ctrl)) return;
         Cs = smem;
-        tail = smem + (size_t)K * p.Dp;
     }
-    float *dcv = tail;
-    float *dgv = dcv + K;
-    int32_t *gs = reinterpret_cast<int32_t *>(dgv + Gp);
+    float *dcv = smem + L.dcv;
+    float *dgv = smem + L.dgv;
+    int32_t *gs = reinterpret_cast<int32_t *>(smem + L.gs);
+    int32_t *sgrp = reinterpret_cast<int32_t *>(smem + L.grp);
+    for (int i = threadIdx.x; i < K; i += kTpThreads) sgrp[i] = p.grp[i];
     for (int i = threadIdx.x; i < K; i += kTpThreads) dcv[i] = p.Dc[(size_t)v * K + i];
     for (int i = threadIdx.x; i < Gp; i += kTpThreads) dgv[i] = p.Dg[(size_t)v * Gp + i];
     for (int i = threadIdx.x; i <= G; i += kTpThreads) gs[i] = p.gstart[i];
@@ -190,8 +211,9 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
             const uint32_t st = p.stamp[n];
             const int wl = (int)stamp_l(st);
             const float lbg_e = __fsub_rd(p.lbg[n], drift_m(p, v, wl));
+            float *lbrow = p.lb + n * Gp;
 
-            float4 xr[DP / 4];
+            ulonglong2 xr[DP / 4];
             load_x<DP>(p, n, xr);
 
             // tighten: exact distance to the own centroid, then the global test again
@@ -206,7 +228,6 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
                 const float da_dn = dist_dn(sa, p);
                 const float *dcw = p.Dc + (size_t)wl * K;
                 const float *dgw = p.Dg + (size_t)wl * Gp;
-                float *lbrow = p.lb + n * Gp;
 
                 float s_best = sa, s_sec = INFINITY, bd_up = ut;
                 int best = a;
@@ -214,7 +235,9 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
                 float bg_val = INFINITY, bg_m1 = INFINITY;  // its bound without / with the best
                 float lmin = INFINITY;            // minimum over the other groups' new bounds
 
-                for (int g = 0; g < G; ++g) {
+                // one group: group filter, then point filter + distances over its
+                // centroids; writes the group's new bound
+                auto visit_group = [&](const int g) {
                     const float lr = lbrow[g];
                     const float le = wl == v ? lr : __fsub_rd(lr, __fsub_ru(dgv[g], __ldg(dgw + g)));
                     const int c_lo = gs[g], c_hi = gs[g + 1];
@@ -244,30 +267,42 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
                             sm1i = a;
                         }
                         bool best_moved = false;
-                        for (int c = c_lo; c < c_hi; ++c) {
-                            if (c == a) continue;
-                            const float pb = wl == v ? lr : __fsub_rd(lr, __fsub_ru(dcv[c], __ldg(dcw + c)));
-                            if (pb >= bd_up) {  // point filter: cannot beat the running best
-                                pm1 = fminf(pm1, pb);
-                                continue;
+                        // windows of up to 32 centroids: first the point-filter test of
+                        // each (independent loads, no branches), then the distances of
+                        // those that pass, in index order
+                        for (int w0 = c_lo; w0 < c_hi; w0 += 32) {
+                            const int wn = min(32, c_hi - w0);
+                            uint32_t pass = 0;
+#pragma unroll 4
+                            for (int j = 0; j < wn; ++j) {
+                                const int c = w0 + j;
+                                const float pb = wl == v ? lr : __fsub_rd(lr, __fsub_ru(dcv[c], __ldg(dcw + c)));
+                                const bool ok = c != a && pb < bd_up;
+                                pass |= ok ? (1u << j) : 0u;
+                                pm1 = (c != a && !ok) ? fminf(pm1, pb) : pm1;
                             }
-                            const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
-                            c_dist += 1;
-                            if (s < s_best || (s == s_best && c < best)) {
-                                s_sec = fminf(s_sec, s_best);
-                                s_best = s;
-                                best = c;
-                                best_moved = true;
-                                bd_up = fminf(bd_up, dist_up(s, p));
-                            } else {
-                                s_sec = fminf(s_sec, s);
-                            }
-                            if (s < sm1) {
-                                sm2 = sm1;
-                                sm1 = s;
-                                sm1i = c;
-                            } else {
-                                sm2 = fminf(sm2, s);
+                            while (pass) {
+                                const int j = __ffs(pass) - 1;
+                                pass &= pass - 1;
+                                const int c = w0 + j;
+                                const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
+                                c_dist += 1;
+                                if (s < s_best || (s == s_best && c < best)) {
+                                    s_sec = fminf(s_sec, s_best);
+                                    s_best = s;
+                                    best = c;
+                                    best_moved = true;
+                                    bd_up = fminf(bd_up, dist_up(s, p));
+                                } else {
+                                    s_sec = fminf(s_sec, s);
+                                }
+                                if (s < sm1) {
+                                    sm2 = sm1;
+                                    sm1 = s;
+                                    sm1i = c;
+                                } else {
+                                    sm2 = fminf(sm2, s);
+                                }
                             }
                         }
                         here = best_moved || (has_a && best == a);
@@ -287,6 +322,33 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
                         lmin = fminf(lmin, val);
                     }
                     lbrow[g] = val;
+                };
+                const int ga = sgrp[a];
+                for (int g0 = 0; g0 < G; g0 += 4) {
+                    // four groups at a time: when none of them survives the group
+                    // filter and none holds the own centroid, their new bounds are
+                    // the drift-adjusted stored ones (one vector load and store)
+                    const float4 lr4 = *reinterpret_cast<const float4 *>(lbrow + g0);
+                    float4 le4 = lr4;
+                    if (wl != v) {
+                        const float4 dv4 = *reinterpret_cast<const float4 *>(dgv + g0);
+                        const float4 dw4 = __ldg(reinterpret_cast<const float4 *>(dgw + g0));
+                        le4.x = __fsub_rd(lr4.x, __fsub_ru(dv4.x, dw4.x));
+                        le4.y = __fsub_rd(lr4.y, __fsub_ru(dv4.y, dw4.y));
+                        le4.z = __fsub_rd(lr4.z, __fsub_ru(dv4.z, dw4.z));
+                        le4.w = __fsub_rd(lr4.w, __fsub_ru(dv4.w, dw4.w));
+                    }
+                    if (g0 + 1 >= G) le4.y = INFINITY;  // padding groups
+                    if (g0 + 2 >= G) le4.z = INFINITY;
+                    if (g0 + 3 >= G) le4.w = INFINITY;
+                    const bool scan = le4.x < bd_up || le4.y < bd_up || le4.z < bd_up || le4.w < bd_up;
+                    if (!scan && (ga < g0 || ga >= g0 + 4)) {
+                        lmin = fminf(lmin, fminf(fminf(le4.x, le4.y), fminf(le4.z, le4.w)));
+                        *reinterpret_cast<float4 *>(lbrow + g0) = le4;
+                    } else {
+                        const int g1 = min(g0 + 4, G);
+                        for (int g = g0; g < g1; ++g) visit_group(g);
+                    }
                 }
                 float lbg_new = bg >= 0 ? fminf(lmin, bg_val) : lmin;
 
@@ -331,14 +393,9 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
     }
 }
 
-template <int DP>
-cudaError_t launch_tp(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit) {
-    const size_t tail = (size_t)p.K * 4 + (size_t)p.Gp * 4 + (size_t)(p.G + 1) * 4;
-    const size_t cbytes = (size_t)p.K * p.Dp * 4;
-    const bool stage = cbytes + tail <= smem_limit && cbytes < (1u << 31);
-    const size_t smem = (stage ? cbytes : 0) + tail;
-    if (smem > smem_limit) return cudaErrorInvalidConfiguration;
-    auto kern = stage ? k_survivor_tp<DP, true> : k_survivor_tp<DP, false>;
+template <int DP, bool STAGE>
+cudaError_t launch_tp2(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem) {
+    auto kern = k_survivor_tp<DP, STAGE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -349,6 +406,17 @@ cudaError_t launch_tp(const Params &p, cudaStream_t s, int respect_done, int num
     count_launch();
     kern<<<(unsigned)grid, kTpThreads, smem, s>>>(p, respect_done);
     return cudaGetLastError();
+}
+
+template <int DP>
+cudaError_t launch_tp(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit) {
+    // stage the centroids in shared memory when they fit
+    const size_t cbytes = (size_t)p.K * p.Dp * 4;
+    const bool stage = TpLayout(p, true).total * 4 <= smem_limit && cbytes < (1u << 31);
+    const size_t smem = TpLayout(p, stage).total * 4;
+    if (smem > smem_limit) return cudaErrorInvalidConfiguration;
+    return stage ? launch_tp2<DP, true>(p, s, respect_done, num_sms, smem)
+                 : launch_tp2<DP, false>(p, s, respect_done, num_sms, smem);
 }
 
 }  // namespace

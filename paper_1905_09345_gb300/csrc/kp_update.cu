@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         ctrl->n_changed = ctrl->n_survivors = ctrl->n_scanned = ctrl->n_dist = ctrl->n_recheck = 0;
         ctrl->queue_count = 0;
         ctrl->moved_count = 0;
+        ctrl->settle_count = 0;
         ctrl->path = KM_PATH_FILTERED;
         ctrl->dense_mode = 0;
         __threadfence();
