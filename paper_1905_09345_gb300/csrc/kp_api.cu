@@ -241,7 +241,7 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
             e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_settle(p, s, first, respect_done, n); });
             if (e != cudaSuccess) return e;
         }
-        return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, first ? 1 : 0, respect_done, n); });
+        return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_cluster_stats(p, s, first ? 1 : 0, respect_done, n); });
     }
     // filtered: global filter, then either the survivor kernel or -- when the
     // filter kernel finds too many survivors -- the dense pass (each of the
@@ -260,7 +260,7 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
         if (e != cudaSuccess) return e;
     }
     // both the survivor kernel and the dense pass append to the moved-point list
-    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, 0, respect_done, n); });
+    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_cluster_stats(p, s, 0, respect_done, n); });
 }
 
 cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {
@@ -424,6 +424,12 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     INIT_CUDA(dalloc(c, &p.label, (size_t)N));
     INIT_CUDA(dalloc(c, &p.moved, (size_t)N));
     INIT_CUDA(dalloc(c, &p.moved_old, (size_t)N));
+    INIT_CUDA(dalloc(c, &p.perm, (size_t)N));
+    INIT_CUDA(dalloc(c, &p.slab, (size_t)N));
+    INIT_CUDA(dalloc(c, &p.hcount, (size_t)K));
+    INIT_CUDA(dalloc(c, &p.hcur, (size_t)K));
+    INIT_CUDA(cudaMemsetAsync(p.hcount, 0, (size_t)K * 4, c->stream));
+    p.hist_smem_k = 8192;
     if (filtered) {
         INIT_CUDA(dalloc(c, &p.u, (size_t)N));
         INIT_CUDA(dalloc(c, &p.lbg, (size_t)N));
@@ -668,6 +674,7 @@ KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
     KP_CUDA(c, cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
     KP_CUDA(c, cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * kStatsCap, s));
     if (p.bcount) KP_CUDA(c, cudaMemsetAsync(p.bcount, 0, (size_t)p.nbucket * 4, s));
+    if (p.hcount) KP_CUDA(c, cudaMemsetAsync(p.hcount, 0, (size_t)p.K * 4, s));
     KP_CUDA(c, cudaStreamSynchronize(s));
     memset(c->ctrl_host, 0, sizeof(Ctrl));
     c->t_host = 0;

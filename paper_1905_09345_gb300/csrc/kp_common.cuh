@@ -52,6 +52,8 @@ struct Ctrl {
     uint32_t filter_ticket;  // last-block-done counter of the filter kernel
     unsigned long long kernels;  // kernels of this context run on the device
     int32_t settle_count;  // rows queued for the exact settle by the tensor-core pass
+    int32_t stats_full;    // the cluster sums of this iteration are recomputed in full
+    uint32_t stats_ticket; // last-block-done counter of k_stats_hist
 };
 
 // every kernel of a context counts itself once (block 0, thread 0)
@@ -105,6 +107,11 @@ struct Params {
     int32_t *bcursor;    // nbucket: next free queue slot of each bucket
     int32_t nbucket, bshift;
     struct SettleReq *sreq;  // N: rows the tensor-core pass left to the exact settle
+    int32_t *perm;       // N: point ids sorted by label (full recompute of the cluster sums)
+    int32_t *slab;       // N: their labels
+    int32_t *hcount;     // K: points per label (zero between uses)
+    int32_t *hcur;       // K: next free slot of each label's segment
+    int32_t hist_smem_k; // largest K whose label histograms live in shared memory
     int32_t *moved;      // N: points whose label changed (dense path)
     int32_t *moved_old;  // N: their previous label (-1: none)
     float *delta;        // K: drift of the last update
@@ -287,6 +294,8 @@ cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint1
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);
+// cluster statistics after an assignment: full recompute or incremental moves
+cudaError_t launch_cluster_stats(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms);
 cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms,
                                int if_dense = 0);
 cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms);

@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(256) k_apply_moves(Params p, int all_points, i
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
     if (if_dense && !*(volatile int *)&ctrl->dense_mode) return;
+    if (*(volatile int *)&ctrl->stats_full) return;  // recomputed in full instead
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -318,14 +319,21 @@ __global__ void __launch_bounds__(256) k_apply_moves(Params p, int all_points, i
         else { n = p.moved[it]; old = p.moved_old[it]; }
         const int nw = p.label[n];
         const float *x = p.X + n * p.D;
-        double q = 0.0;
+        // ||x||^2 as an FP32 pair (exact squares, compensated sum): FP64
+        // arithmetic is slow on these SMs; only the atomics are FP64
+        float qh = 0.f, ql = 0.f;
         for (int i = lane; i < p.D; i += 32) {
-            double xi = (double)__ldg(x + i);
-            q += xi * xi;
+            const float xf = __ldg(x + i);
+            const float sq = __fmul_rn(xf, xf);
+            const float s = __fadd_rn(qh, sq), bb = __fsub_rn(s, qh);
+            const float e = __fadd_rn(__fsub_rn(qh, __fsub_rn(s, bb)), __fsub_rn(sq, bb));
+            ql = __fadd_rn(ql, __fadd_rn(e, __fmaf_rn(xf, xf, -sq)));
+            qh = s;
+            const double xi = (double)xf;
             atomicAdd(&p.S[(size_t)nw * p.D + i], xi);
             if (old >= 0) atomicAdd(&p.S[(size_t)old * p.D + i], -xi);
         }
-        q = warp_sum_d(q);
+        const double q = warp_sum_d((double)qh + (double)ql);
         if (lane == 0) {
             atomicAdd(&p.Q[nw], q);
             atomicAdd(&p.cnt[nw], 1ull);

@@ -1,0 +1,266 @@
+// kp_stats.cu -- cluster statistics (S_k = sum x in FP64, Q_k = sum ||x||^2,
+// n_k) for the centroid update.
+//
+// Two ways, chosen on the device after each assignment:
+//   * incremental (few labels changed): k_apply_moves moves each relabelled
+//     point's coordinates from its old cluster's sums to its new one's;
+//   * full recompute (iteration 0, or more than N/16 labels changed): the
+//     points are sorted by label (a counting sort: k_stats_hist counts and
+//     lays out the segments, k_stats_scatter places the point ids), then each
+//     warp sums a run of 64 sorted points coordinate-parallel in FP64 and
+//     adds one partial per cluster it met to the global sums.  Global FP64
+//     atomics then touch each cluster a few times instead of once per point,
+//     which is what made the per-point update slow when every point moves.
+#include "kp_common.cuh"
+
+namespace kp {
+
+constexpr int kStatsThreads = 256;
+constexpr int kStatsTile = kStatsThreads * 4;  // points per block step of the scatter
+constexpr int kSumRun = 64;                    // sorted points per warp in k_stats_sum
+constexpr int kSumMaxPer = 8;                  // coordinates per lane (D <= 256)
+
+__device__ __forceinline__ bool stats_full_rule(const Params &p, int all_points) {
+    return all_points || (int64_t)p.ctrl->moved_count * 16 > p.N;
+}
+
+// Decide the mode; in full mode zero S and Q, count the labels per cluster
+// (shared-memory histogram when K fits), and let the last block turn the
+// counts into segment offsets (hcur) and the new cluster sizes (cnt).
+__global__ void __launch_bounds__(kStatsThreads) k_stats_hist(Params p, int all_points, int respect_done) {
+    extern __shared__ int hist[];
+    __shared__ int last;
+    __shared__ int wsum[kStatsThreads / 32];
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    const bool full = stats_full_rule(p, all_points);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->stats_full = full ? 1 : 0;
+    if (!full) return;
+    const int K = p.K, D = p.D;
+    const bool local = K <= p.hist_smem_k;
+    const int64_t tid = (int64_t)blockIdx.x * kStatsThreads + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * kStatsThreads;
+    for (int64_t i = tid; i < (int64_t)K * D; i += nthr) p.S[i] = 0.0;
+    for (int64_t i = tid; i < K; i += nthr) p.Q[i] = 0.0;
+    if (local) {
+        for (int i = threadIdx.x; i < K; i += kStatsThreads) hist[i] = 0;
+        __syncthreads();
+    }
+    for (int64_t n = tid; n < p.N; n += nthr) {
+        const int k = p.label[n];
+        if (local) atomicAdd(&hist[k], 1);
+        else atomicAdd(&p.hcount[k], 1);
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += kStatsThreads)
+            if (hist[i]) atomicAdd(&p.hcount[i], hist[i]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->stats_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // exclusive scan of the counts: each thread a contiguous run
+    const int lane = threadIdx.x & 31;
+    const int per = (K + kStatsThreads - 1) / kStatsThreads;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, K);
+    int run = 0;
+    for (int b = b0; b < b1; ++b) run += __ldcg(p.hcount + b);
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    int off = incl - run;
+    for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) off += wsum[w];
+    for (int b = b0; b < b1; ++b) {
+        const int c = __ldcg(p.hcount + b);
+        p.hcur[b] = off;
+        p.cnt[b] = (unsigned long long)c;
+        p.hcount[b] = 0;  // ready for the next full recompute
+        off += c;
+    }
+    if (threadIdx.x == 0) ctrl->stats_ticket = 0;
+}
+
+// Full mode: place every point id in its cluster's segment (per tile of 1024
+// points: shared-memory counts, one global atomic per cluster and tile).
+__global__ void __launch_bounds__(kStatsThreads) k_stats_scatter(Params p, int respect_done) {
+    extern __shared__ int sh[];  // K counters | K bases
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (!*(volatile int *)&ctrl->stats_full) return;
+    const int K = p.K;
+    const bool local = K <= p.hist_smem_k;
+    if (!local) {  // large K: one global atomic per point
+        for (int64_t n = (int64_t)blockIdx.x * kStatsThreads + threadIdx.x; n < p.N;
+             n += (int64_t)gridDim.x * kStatsThreads) {
+            const int k = p.label[n];
+            const int pos = atomicAdd(&p.hcur[k], 1);
+            p.perm[pos] = (int32_t)n;
+            p.slab[pos] = k;
+        }
+        return;
+    }
+    int *cnt = sh;
+    int *base = sh + K;
+    for (int i = threadIdx.x; i < K; i += kStatsThreads) cnt[i] = 0;
+    __syncthreads();
+    for (int64_t t0 = (int64_t)blockIdx.x * kStatsTile; t0 < p.N; t0 += (int64_t)gridDim.x * kStatsTile) {
+        int k[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t n = t0 + j * kStatsThreads + threadIdx.x;
+            k[j] = n < p.N ? p.label[n] : -1;
+            if (k[j] >= 0) atomicAdd(&cnt[k[j]], 1);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += kStatsThreads) {
+            const int c = cnt[i];
+            base[i] = c ? atomicAdd(&p.hcur[i], c) : 0;
+            cnt[i] = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (k[j] >= 0) {
+                const int pos = base[k[j]] + atomicAdd(&cnt[k[j]], 1);
+                p.perm[pos] = (int32_t)(t0 + j * kStatsThreads + threadIdx.x);
+                p.slab[pos] = k[j];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += kStatsThreads) cnt[i] = 0;
+        __syncthreads();
+    }
+}
+
+// Error-free transformation of a sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Full mode: each warp sums kSumRun consecutive sorted points, lanes over the
+// coordinates, eight points' loads in flight at a time, and adds its partial
+// sums to S and Q whenever the cluster changes along the run (and at its end).
+// FP64 arithmetic is slow on the SMs of this GPU, so the run sums are kept as
+// unevaluated FP32 pairs (hi + lo, compensated summation with TwoSum; the
+// squares split exactly with a fused multiply-add), accurate to a few units
+// in 2^-48 relative for runs this short, and turned into FP64 only when they
+// are added to the global sums.
+template <int NPER>  // coordinates per lane: ceil(D / 32)
+__global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respect_done) {
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    if (!*(volatile int *)&ctrl->stats_full) return;
+    const int D = p.D;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * kStatsThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kStatsThreads) >> 5;
+    constexpr int kB = 8;  // points per batch
+    for (int64_t r0 = warp * kSumRun; r0 < p.N; r0 += nwarps * kSumRun) {
+        const int64_t r1 = min(r0 + kSumRun, p.N);
+        float sh[NPER], sl[NPER];
+#pragma unroll
+        for (int j = 0; j < NPER; ++j) sh[j] = sl[j] = 0.f;
+        float qh = 0.f, ql = 0.f;
+        int cur = p.slab[r0];
+        auto flush = [&]() {
+            const double qs = warp_sum_d((double)qh + (double)ql);
+#pragma unroll
+            for (int j = 0; j < NPER; ++j) {
+                const int i = lane + 32 * j;
+                const double v = (double)sh[j] + (double)sl[j];
+                if (i < D && v != 0.0) atomicAdd(&p.S[(size_t)cur * D + i], v);
+                sh[j] = sl[j] = 0.f;
+            }
+            if (lane == 0 && qs != 0.0) atomicAdd(&p.Q[cur], qs);
+            qh = ql = 0.f;
+        };
+        for (int64_t rb = r0; rb < r1; rb += kB) {
+            int nb[kB], kb[kB];
+            float xv[kB][NPER];
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+                const bool ok = rb + b < r1;
+                nb[b] = ok ? p.perm[rb + b] : 0;
+                kb[b] = ok ? p.slab[rb + b] : -1;
+            }
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+                const float *x = p.X + (int64_t)nb[b] * D;
+#pragma unroll
+                for (int j = 0; j < NPER; ++j) {
+                    const int i = lane + 32 * j;
+                    xv[b][j] = (kb[b] >= 0 && i < D) ? __ldg(x + i) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < kB; ++b) {
+                if (kb[b] < 0) break;
+                if (kb[b] != cur) {  // warp-uniform
+                    flush();
+                    cur = kb[b];
+                }
+#pragma unroll
+                for (int j = 0; j < NPER; ++j) {
+                    const float xi = xv[b][j];
+                    float s, e;
+                    two_sum(sh[j], xi, s, e);
+                    sh[j] = s;
+                    sl[j] = __fadd_rn(sl[j], e);
+                    const float sq = __fmul_rn(xi, xi);
+                    const float sqe = __fmaf_rn(xi, xi, -sq);  // exact: xi^2 == sq + sqe
+                    two_sum(qh, sq, s, e);
+                    qh = s;
+                    ql = __fadd_rn(ql, __fadd_rn(e, sqe));
+                }
+            }
+        }
+        flush();
+    }
+}
+
+bool stats_full_supported(const Params &p) { return p.perm != nullptr && p.D <= 32 * kSumMaxPer; }
+
+cudaError_t launch_cluster_stats(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms) {
+    if (stats_full_supported(p)) {
+        const size_t h1 = p.K <= p.hist_smem_k ? (size_t)p.K * 4 : 0;
+        const size_t h2 = 2 * h1;
+        cudaError_t e = cudaFuncSetAttribute(k_stats_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h2);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = (p.N + kStatsTile - 1) / kStatsTile;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms * 8));
+        count_launch();
+        k_stats_hist<<<grid, kStatsThreads, h1, s>>>(p, all_points, respect_done);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count_launch();
+        k_stats_scatter<<<grid, kStatsThreads, h2, s>>>(p, respect_done);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int64_t runs = (p.N + kSumRun - 1) / kSumRun;
+        const unsigned sgrid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>((runs + kStatsThreads / 32 - 1) / (kStatsThreads / 32), (int64_t)num_sms * 8));
+        count_launch();
+        const int nper = (p.D + 31) / 32;
+        if (nper <= 1) k_stats_sum<1><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
+        else if (nper <= 2) k_stats_sum<2><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
+        else if (nper <= 4) k_stats_sum<4><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
+        else k_stats_sum<kSumMaxPer><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // the incremental update runs only when k_stats_hist chose it
+        return launch_apply_moves(p, s, 0, respect_done, num_sms);
+    }
+    return launch_apply_moves(p, s, all_points, respect_done, num_sms);
+}
+
+}  // namespace kp
