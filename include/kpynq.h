@@ -115,7 +115,9 @@ enum {
     KM_KERNEL_SURVIVOR = 3, /* group/point filter + survivor distances */
     KM_KERNEL_UPDATE = 4,   /* centroid update, drift, objective */
     KM_KERNEL_OTHER = 5,    /* loop control, rebase, bounds export */
-    KM_KERNEL_KINDS = 6
+    KM_KERNEL_SETTLE = 6,   /* exact settle of the tensor-core pass's near-ties */
+    KM_KERNEL_STATS = 7,    /* full recompute of the cluster sums (label sort) */
+    KM_KERNEL_KINDS = 8
 };
 
 /* kmeans_iter_stats.path */
@@ -191,7 +193,9 @@ KM_API int kmeans_get_labels(kmeans_ctx *ctx, int32_t *labels);
 KM_API int kmeans_get_centroids(kmeans_ctx *ctx, float *C);
 
 /* Statistics of iteration t (0 <= t < iterations run so far, at most the
- * last 4096 iterations are kept). */
+ * last 4096 iterations are kept).  t = -1: the final assignment of the last
+ * kmeans_fit (its path, label changes, distances and objective; iter is the
+ * number of iterations that fit ran); KM_ESTATE before any fit. */
 KM_API int kmeans_get_stats(kmeans_ctx *ctx, int32_t t, kmeans_iter_stats *stats);
 
 /*

@@ -42,6 +42,7 @@ struct kmeans_ctx {
     float *X_own = nullptr;
     int tcap = 0;
     bool use_tc = false;   // dense passes on the tensor cores
+    bool have_final = false;  // a fit finished: its final-assignment record is kept
     int t_host = 0;        // iterations run (mirrors ctrl->t after each call)
     int v_host = 0;        // table version (mirrors ctrl->v)
     bool broken = false;
@@ -228,6 +229,18 @@ int ensure_tables(kmeans_ctx *c, int need) {
 }
 
 // One assignment (dense when `dense`, filtered otherwise), stream-ordered.
+// Cluster statistics after an assignment: the full recompute (when the device
+// chooses it) and the incremental moves (otherwise).
+cudaError_t enqueue_stats(kmeans_ctx *c, const Params &p, cudaStream_t s, int all_points, int respect_done) {
+    const int n = c->num_sms;
+    if (stats_full_supported(p)) {
+        cudaError_t e = timed(c, s, KM_KERNEL_STATS, [&] { return launch_stats_full(p, s, all_points, respect_done, n); });
+        if (e != cudaSuccess) return e;
+        all_points = 0;  // the full recompute covers iteration 0
+    }
+    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, all_points, respect_done, n); });
+}
+
 cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool dense, bool first, int respect_done) {
     cudaError_t e;
     const int n = c->num_sms;
@@ -238,10 +251,10 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
         });
         if (e != cudaSuccess) return e;
         if (c->use_tc) {
-            e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_settle(p, s, first, respect_done, n); });
+            e = timed(c, s, KM_KERNEL_SETTLE, [&] { return launch_settle(p, s, first, respect_done, n); });
             if (e != cudaSuccess) return e;
         }
-        return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_cluster_stats(p, s, first ? 1 : 0, respect_done, n); });
+        return enqueue_stats(c, p, s, first ? 1 : 0, respect_done);
     }
     // filtered: global filter, then either the survivor kernel or -- when the
     // filter kernel finds too many survivors -- the dense pass (each of the
@@ -256,11 +269,11 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
     });
     if (e != cudaSuccess) return e;
     if (c->use_tc) {  // no rows queued unless the dense pass ran
-        e = timed(c, s, KM_KERNEL_DENSE, [&] { return launch_settle(p, s, 0, respect_done, n); });
+        e = timed(c, s, KM_KERNEL_SETTLE, [&] { return launch_settle(p, s, 0, respect_done, n); });
         if (e != cudaSuccess) return e;
     }
     // both the survivor kernel and the dense pass append to the moved-point list
-    return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_cluster_stats(p, s, 0, respect_done, n); });
+    return enqueue_stats(c, p, s, 0, respect_done);
 }
 
 cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {
@@ -456,7 +469,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.grp = grp;
     p.gstart = gstart;
     INIT_CUDA(dalloc(c, &p.ctrl, 1));
-    INIT_CUDA(dalloc(c, &p.stats, (size_t)kStatsCap));
+    INIT_CUDA(dalloc(c, &p.stats, (size_t)kStatsCap + 1));  // + the final assignment
     INIT_CUDA(dalloc(c, &c->flag_dev, 1));
     c->tcap = 64;
     INIT_CUDA(dalloc(c, &p.Dc, (size_t)c->tcap * K));
@@ -475,7 +488,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     INIT_CUDA(cudaMemsetAsync(p.Dg, 0, (size_t)c->tcap * p.Gp * 4, s));
     INIT_CUDA(cudaMemsetAsync(p.Dm, 0, (size_t)c->tcap * 4, s));
     INIT_CUDA(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
-    INIT_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * kStatsCap, s));
+    INIT_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * (kStatsCap + 1), s));
 
     // contiguous grouping: centroid j -> floor(j G / K)
     std::vector<int32_t> hg(K), hs(G + 1);
@@ -580,6 +593,7 @@ KM_API int kmeans_fit(kmeans_ctx *c, int32_t max_iter, double tol, int32_t *labe
                                      cudaMemcpyDefault, s));
     if (objective) KP_CUDA(c, cudaMemcpyAsync(objective, &p.ctrl->jfinal, 8, cudaMemcpyDefault, s));
     KP_CUDA(c, cudaStreamSynchronize(s));
+    c->have_final = true;
     if (n_iter) {
         int32_t ni = c->ctrl_host->fit_n_iter;
         if (is_device_ptr(n_iter)) KP_CUDA(c, cudaMemcpy(n_iter, &ni, 4, cudaMemcpyHostToDevice));
@@ -614,10 +628,14 @@ KM_API int kmeans_get_stats(kmeans_ctx *c, int32_t t, kmeans_iter_stats *stats) 
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!stats) return set_err(c, KM_EINVAL, "stats is NULL");
-    if (t < 0 || t >= c->t_host || t < c->t_host - kStatsCap)
+    if (t == -1) {
+        if (!c->have_final) return set_err(c, KM_ESTATE, "no kmeans_fit has finished");
+    } else if (t < 0 || t >= c->t_host || t < c->t_host - kStatsCap) {
         return set_err(c, KM_EINVAL, "no statistics kept for iteration %d", t);
+    }
     DeviceGuard dg(c->dev);
-    KP_CUDA(c, cudaMemcpyAsync(stats, c->p.stats + (t % kStatsCap), sizeof(*stats), cudaMemcpyDefault, c->stream));
+    const size_t slot = t == -1 ? (size_t)kStatsCap : (size_t)(t % kStatsCap);
+    KP_CUDA(c, cudaMemcpyAsync(stats, c->p.stats + slot, sizeof(*stats), cudaMemcpyDefault, c->stream));
     KP_CUDA(c, cudaStreamSynchronize(c->stream));
     return KM_OK;
 }
@@ -672,12 +690,13 @@ KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
     KP_CUDA(c, cudaMemsetAsync(p.Dg, 0, (size_t)c->tcap * p.Gp * 4, s));
     KP_CUDA(c, cudaMemsetAsync(p.Dm, 0, (size_t)c->tcap * 4, s));
     KP_CUDA(c, cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
-    KP_CUDA(c, cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * kStatsCap, s));
+    KP_CUDA(c, cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * (kStatsCap + 1), s));
     if (p.bcount) KP_CUDA(c, cudaMemsetAsync(p.bcount, 0, (size_t)p.nbucket * 4, s));
     if (p.hcount) KP_CUDA(c, cudaMemsetAsync(p.hcount, 0, (size_t)p.K * 4, s));
     KP_CUDA(c, cudaStreamSynchronize(s));
     memset(c->ctrl_host, 0, sizeof(Ctrl));
     c->t_host = 0;
+    c->have_final = false;
     c->v_host = 0;
     for (int k = 0; k < KM_KERNEL_KINDS; ++k) {
         c->prof_ms[k] = 0.0;

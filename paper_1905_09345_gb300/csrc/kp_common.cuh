@@ -67,10 +67,8 @@ struct SettleReq {
     int32_t n;       // point
     int32_t old;     // label before this pass (-1: none)
     int32_t i1;      // tensor-core winner (the bounds were written for it)
-    int32_t nc;      // window columns found (> 4: overflow, all K are candidates)
-    uint32_t pack;   // up to four window columns, 8 bits each, first found highest
     float lb_alt;    // group bound that holds for every column (from the smallest estimate)
-    int32_t pad0, pad1;
+    unsigned long long gmask;  // groups that can hold the winner (all ones: every group)
 };
 
 // Everything a kernel needs, passed by value.
@@ -294,8 +292,10 @@ cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint1
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);
-// cluster statistics after an assignment: full recompute or incremental moves
-cudaError_t launch_cluster_stats(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms);
+// full recompute of the cluster statistics (k_stats_hist decides on the
+// device; k_apply_moves then skips itself); needs the label-sort buffers
+bool stats_full_supported(const Params &p);
+cudaError_t launch_stats_full(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms);
 cudaError_t launch_apply_moves(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms,
                                int if_dense = 0);
 cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms);

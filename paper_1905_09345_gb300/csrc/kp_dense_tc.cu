@@ -409,45 +409,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             row[cur_g] = gm1;
             const float thr = __fadd_ru(b1, twoE);
 
-            // Rows whose runner-up is inside the error window are settled
-            // exactly by k_settle afterwards: a rescan of the accumulators
-            // collects the window's columns (up to four ids packed in one
-            // register; more is an overflow that k_settle answers with all K),
-            // and the row goes to the settle queue.  The epilogue writes such a
+            // Rows whose runner-up is inside the error window go to the settle
+            // queue: k_settle decides them exactly afterwards from FP32 (and
+            // FP64) distances to the centroids of the groups whose minimum lies
+            // in the window (every other centroid is strictly farther than the
+            // tensor-core winner i1, which is among them).  The epilogue writes such a
             // row's bounds as if the tensor-core winner i1 won; k_settle
             // corrects them when it does not.
             const int old = valid ? (first ? -1 : p.label[n]) : -1;
             const bool need = valid && b2 <= thr;
-            if (__any_sync(0xffffffffu, need)) {
-                uint32_t pack = 0;
-                int nc = 0;
-                for (int c0 = 0; c0 < Kp; c0 += 32) {
-                    uint32_t rr[32];
-                    tmem_ld32(tb + c0, rr);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float t = fmaf(-2.f, __uint_as_float(rr[j]), cn[c0 + j]);
-                        const bool in = need && t <= thr;
-                        pack = in ? (pack << 8) | (uint32_t)(c0 + j) : pack;
-                        nc += in;
-                    }
-                }
+            {
                 const unsigned nm = __ballot_sync(0xffffffffu, need);
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&ctrl->settle_count, __popc(nm));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (need) {
-                    SettleReq q;
-                    q.n = (int32_t)n;
-                    q.old = old;
-                    q.i1 = i1;
-                    q.nc = nc;
-                    q.pack = pack;
-                    // every column is at least b1: when i1 loses, this bounds both
-                    // i1's group (which now keeps i1) and the winner's group
-                    q.lb_alt = sqrt_dn(__fsub_rd(__fadd_rd(xlo, b1), E));
-                    q.pad0 = q.pad1 = 0;
-                    p.sreq[base + __popc(nm & ((1u << lane) - 1u))] = q;
+                if (nm) {
+                    // the groups that can hold a window column: group minimum
+                    // within the window (at most 64 groups; more: all of them)
+                    unsigned long long gmask = ~0ull;
+                    if (G <= 64) {
+                        gmask = 0ull;
+                        for (int g = 0; g < G; ++g) gmask |= (row[g] <= thr) ? (1ull << g) : 0ull;
+                    }
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&ctrl->settle_count, __popc(nm));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (need) {
+                        SettleReq q;
+                        q.n = (int32_t)n;
+                        q.old = old;
+                        q.i1 = i1;
+                        // every column is at least b1: when i1 loses, this bounds both
+                        // i1's group (which now keeps i1) and the winner's group
+                        q.lb_alt = sqrt_dn(__fsub_rd(__fadd_rd(xlo, b1), E));
+                        q.gmask = gmask;
+                        p.sreq[base + __popc(nm & ((1u << lane) - 1u))] = q;
+                    }
                 }
             }
             // accumulators no longer needed
@@ -524,73 +518,112 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---------------------------------------------------------------------------
 // k_settle: the exact decision for the rows the tensor-core epilogue queued
 // (runner-up inside the error window).  One warp per row, lanes over the
-// coordinates: FP32 direct-difference distances of the window's candidates
-// (in ascending index order; every other centroid is strictly farther than
-// the tensor-core winner), FP64 with the summation order of the FP64
-// definition where FP32 cannot separate them.  Writes the label, corrects
-// u / lb / lbg when the winner is not i1, and appends label changes to the
-// moved-point list.
+// candidate centroids (those of the groups whose tensor-core minimum lies in
+// the window; C staged in shared memory, the row in registers): the FP32
+// direct-difference distances, the smallest with the lowest index, and where
+// FP32 cannot separate it from the runner-up, FP64 with the summation order
+// of the FP64 definition among the unresolved ones.
+// Writes the label, corrects u / lb / lbg when the winner is not i1, and
+// appends label changes to the moved-point list.
 // ---------------------------------------------------------------------------
+constexpr int kSettleThreads = 256;
+
 template <int D>
-__global__ void __launch_bounds__(256) k_settle(Params p, int first, int respect_done) {
+__global__ void __launch_bounds__(kSettleThreads) k_settle(Params p, int first, int respect_done) {
+    extern __shared__ __align__(128) float sm_settle[];  // C (K x Dp) | per-warp row (D)
+    __shared__ __align__(8) uint64_t bar;
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
     const int count = *(volatile int *)&ctrl->settle_count;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int warp_in = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * (kSettleThreads / 32) + warp_in;
+    const int64_t nwarps = (int64_t)gridDim.x * (kSettleThreads / 32);
+    if ((int64_t)blockIdx.x * (kSettleThreads / 32) >= count) return;  // uniform per block
+    const int K = p.K;
+    if (!stage_to_smem(sm_settle, p.C, (uint32_t)((size_t)K * p.Dp * 4), &bar, ctrl)) return;
+    const float *Cs = sm_settle;
+    float *xs = sm_settle + (size_t)K * p.Dp + warp_in * D;
+    int32_t *gs_s = reinterpret_cast<int32_t *>(sm_settle + (size_t)K * p.Dp + (kSettleThreads / 32) * D);
+    for (int i = threadIdx.x; i <= p.G; i += kSettleThreads) gs_s[i] = p.gstart[i];
+    __syncthreads();
     const bool bounds = p.algo == KM_ALGO_FILTERED;
-    constexpr int kPer = D / 32;
     unsigned long long c_changed = 0, c_recheck = 0;
     for (int64_t it = warp; it < count; it += nwarps) {
         const SettleReq q = p.sreq[it];
         const int64_t n = q.n;
-        float xv[kPer];
+        for (int i = lane; i < D / 4; i += 32)
+            reinterpret_cast<float4 *>(xs)[i] = __ldg(reinterpret_cast<const float4 *>(p.X + n * D) + i);
+        __syncwarp();
+        // the row as packed FP32 pairs in registers; distances with packed
+        // FP32x2 subtract / fused multiply-add (each lane of a pair an ordinary
+        // round-to-nearest FP32 operation; four partial sums of D/4 terms)
+        ulonglong2 xr[D / 4];
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) xv[j] = __ldg(p.X + n * D + lane + 32 * j);
-        const int m = q.nc > 4 ? p.K : q.nc;  // overflow: every centroid
-        auto cand = [&](int k) { return q.nc > 4 ? k : (int)((q.pack >> (8 * (q.nc - 1 - k))) & 0xffu); };
+        for (int i = 0; i < D / 4; ++i) xr[i] = reinterpret_cast<const ulonglong2 *>(xs)[i];
         auto fp32 = [&](int col) {
-            const float *c = p.C + (size_t)col * p.Dp;
-            float a = 0.f;
+            const ulonglong2 *c = reinterpret_cast<const ulonglong2 *>(Cs + (size_t)col * p.Dp);
+            unsigned long long a0 = 0ull, a1 = 0ull;
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
-                const float t = xv[j] - __ldg(c + lane + 32 * j);
-                a = fmaf(t, t, a);
+            for (int i = 0; i < D / 4; ++i) {
+                const ulonglong2 c2 = c[i];
+                unsigned long long d0, d1;
+                asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(xr[i].x), "l"(c2.x));
+                asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(xr[i].y), "l"(c2.y));
+                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
+                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            return a;
+            float l0, h0, l1, h1;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(h0) : "l"(a0));
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(l1), "=f"(h1) : "l"(a1));
+            return (l0 + h0) + (l1 + h1);
         };
-        float bs = INFINITY, sec = INFINITY;
-        int bi = q.i1;
-        for (int k = 0; k < m; ++k) {
-            const int col = cand(k);
-            const float sx = fp32(col);
-            if (sx < bs || (sx == bs && col < bi)) {
-                sec = bs;
-                bs = sx;
-                bi = col;
-            } else if (sx < sec) {
-                sec = sx;
+        // the candidates: the centroids of the masked groups, lanes over the
+        // centroids of one group at a time (ascending index); all K when the
+        // mask holds every group
+        const int G = p.G;
+        auto for_candidates = [&](auto &&fn) {
+            if (q.gmask == ~0ull) {
+                for (int col = lane; col < K; col += 32) fn(col);
+                return;
             }
-        }
+            unsigned long long m = q.gmask;
+            while (m) {
+                const int g = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                if (g >= G) break;
+                for (int col = gs_s[g] + lane; col < gs_s[g + 1]; col += 32) fn(col);
+            }
+        };
+        // each lane: its candidates' two smallest; then the warp's winner and runner-up
+        float s1 = INFINITY, s2 = INFINITY;
+        int i1 = 0x7fffffff;
+        for_candidates([&](int col) {
+            const float sx = fp32(col);
+            if (sx < s1 || (sx == s1 && col < i1)) {
+                s2 = s1;
+                s1 = sx;
+                i1 = col;
+            } else {
+                s2 = fminf(s2, sx);
+            }
+        });
+        float bs = s1;
+        int bi = i1;
+        warp_argmin(bs, bi);
+        const float sec = warp_min(i1 == bi ? s2 : s1);
         if (sec != INFINITY && unresolved(bs, sec, p)) {
             double bd = INFINITY;
-            int bj = bi;
-            for (int k = 0; k < m; ++k) {
-                const int col = cand(k);
-                if (!unresolved(bs, fp32(col), p)) continue;
-                if (lane == 0) {
-                    const double d64 = dist2_f64(p.X + n * D, p.C + (size_t)col * p.Dp, D);
-                    if (d64 < bd || (d64 == bd && col < bj)) {
-                        bd = d64;
-                        bj = col;
-                    }
+            int bj = 0x7fffffff;
+            for_candidates([&](int col) {
+                if (!unresolved(bs, fp32(col), p)) return;
+                const double d64 = dist2_f64(xs, Cs + (size_t)col * p.Dp, D);
+                if (d64 < bd || (d64 == bd && col < bj)) {
+                    bd = d64;
+                    bj = col;
                 }
-            }
-            bj = __shfl_sync(0xffffffffu, bj, 0);
+            });
+            warp_argmin_d(bd, bj);
             if (bj != bi) bs = fp32(bj);
             bi = bj;
             c_recheck += 1;
@@ -614,6 +647,7 @@ __global__ void __launch_bounds__(256) k_settle(Params p, int first, int respect
                 }
             }
         }
+        __syncwarp();  // the row buffer is reused
     }
     if (lane == 0) {
         if (c_changed) atomicAdd(&ctrl->n_changed, c_changed);
@@ -730,11 +764,16 @@ cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_don
 }  // namespace
 
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms) {
+    const size_t smem = (size_t)p.K * p.Dp * 4 + (size_t)(kSettleThreads / 32) * p.D * 4 + (size_t)(p.G + 1) * 4;
+    auto kern = p.D == 64 ? k_settle<64> : k_settle<128>;
+    if (p.D != 64 && p.D != 128) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSettleThreads, smem);
+    if (e != cudaSuccess) return e;
     count_launch();
-    const unsigned grid = (unsigned)num_sms * 8;
-    if (p.D == 64) k_settle<64><<<grid, 256, 0, s>>>(p, first, respect_done);
-    else if (p.D == 128) k_settle<128><<<grid, 256, 0, s>>>(p, first, respect_done);
-    else return cudaErrorInvalidValue;
+    kern<<<(unsigned)(num_sms * std::max(per_sm, 1)), kSettleThreads, smem, s>>>(p, first, respect_done);
     return cudaGetLastError();
 }
 

@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respe
 
 bool stats_full_supported(const Params &p) { return p.perm != nullptr && p.D <= 32 * kSumMaxPer; }
 
-cudaError_t launch_cluster_stats(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms) {
-    if (stats_full_supported(p)) {
+cudaError_t launch_stats_full(const Params &p, cudaStream_t s, int all_points, int respect_done, int num_sms) {
+    {
         const size_t h1 = p.K <= p.hist_smem_k ? (size_t)p.K * 4 : 0;
         const size_t h2 = 2 * h1;
         cudaError_t e = cudaFuncSetAttribute(k_stats_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h2);
@@ -256,11 +256,8 @@ cudaError_t launch_cluster_stats(const Params &p, cudaStream_t s, int all_points
         else if (nper <= 2) k_stats_sum<2><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
         else if (nper <= 4) k_stats_sum<4><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
         else k_stats_sum<kSumMaxPer><<<sgrid, kStatsThreads, 0, s>>>(p, respect_done);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // the incremental update runs only when k_stats_hist chose it
-        return launch_apply_moves(p, s, 0, respect_done, num_sms);
+        return cudaGetLastError();
     }
-    return launch_apply_moves(p, s, all_points, respect_done, num_sms);
 }
 
 }  // namespace kp

@@ -112,6 +112,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         st.objective = J;
         if (final_only) {
             ctrl->jfinal = J;
+            st.done = 1;
+            p.stats[kStatsCap] = st;  // the final assignment's record
         } else {
             p.Dm[v + 1] = __fadd_ru(p.Dm[v], dm);
             st.max_drift = (double)dm;

@@ -20,8 +20,9 @@ KM_ALGO_FILTERED, KM_ALGO_LLOYD = 0, 1
 KM_GROUP_CONTIGUOUS = 0
 KM_DENSE_AUTO, KM_DENSE_FP32 = 0, 1
 KM_PATH_FILTERED, KM_PATH_DENSE_FP32, KM_PATH_DENSE_TC = 0, 1, 2
-KM_KERNEL_DENSE, KM_KERNEL_MOVES, KM_KERNEL_FILTER, KM_KERNEL_SURVIVOR, KM_KERNEL_UPDATE, KM_KERNEL_OTHER = range(6)
-KERNEL_KIND_NAMES = ["dense_assign", "apply_moves", "filter", "survivor", "update", "other"]
+(KM_KERNEL_DENSE, KM_KERNEL_MOVES, KM_KERNEL_FILTER, KM_KERNEL_SURVIVOR, KM_KERNEL_UPDATE, KM_KERNEL_OTHER,
+ KM_KERNEL_SETTLE, KM_KERNEL_STATS) = range(8)
+KERNEL_KIND_NAMES = ["dense_assign", "apply_moves", "filter", "survivor", "update", "other", "settle", "stats"]
 STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ENOMEM", -3: "KM_ECUDA", -4: "KM_ETIMEOUT",
                 -5: "KM_ESTATE"}
 
@@ -283,6 +284,11 @@ class KMeans:
         n_iter, J = kmeans_fit(self.ctx, max_iter, tol, labels, centroids)
         stats = self.stats(t0, t0 + n_iter) if with_stats else None
         return FitResult(labels, centroids, J, n_iter, stats)
+
+    def final_stats(self) -> dict:
+        """Statistics of the last fit's final assignment (its path, label
+        changes, distance evaluations and objective)."""
+        return kmeans_get_stats(self.ctx, -1)
 
     def stats(self, t0: int, t1: int) -> list:
         """Per-iteration statistics of iterations t0 .. t1-1."""
