@@ -371,3 +371,48 @@ def test_aniso_full_size(kp, aniso):
     assert abs(r.objective - J) <= OBJECTIVE_RTOL * J
     assert all(s["path"] in (kp.KM_PATH_FILTERED, kp.KM_PATH_DENSE_TC) for s in r.stats)
     km.close()
+
+
+def test_tensor_core_settle_many_groups(kp):
+    """More than 64 groups: the tensor-core pass cannot name the window's
+    groups in its 64-bit mask, so the settle kernel scans every centroid.
+    Points near the midpoints of centroid pairs keep it busy."""
+    rng = np.random.default_rng(21)
+    N, D, K, G = 6000, 64, 256, 80
+    C0 = (rng.uniform(-3, 3, (K, D)) + 25.0).astype(np.float32)
+    a = rng.integers(0, K, N)
+    b = (a + 1 + rng.integers(0, K - 1, N)) % K
+    w = (0.5 + rng.uniform(-1e-3, 1e-3, N))[:, None]
+    X = (w * C0[a] + (1 - w) * C0[b] + rng.normal(0, 1e-2, (N, D))).astype(np.float32)
+    st = lockstep(kp, X, C0, G, 3, dense_switch=1e-6)  # dense in every iteration
+    assert all(s["path"] == kp.KM_PATH_DENSE_TC for s in st)
+
+
+def test_survivor_centroids_not_staged(kp):
+    """K x D too large for the survivor kernel to stage the centroids in
+    shared memory (1024 x 68 floats): the filtered path reads them from
+    global memory."""
+    rng = np.random.default_rng(22)
+    N, D, K, G = 8000, 64, 1024, 100
+    X, _ = synth.gaussian_mixture(rng, N, D, 256, centre_range=8.0, scale="fixed", scale_args=(1.0,))
+    C0 = synth.sample_init(rng, X, K)
+    st = lockstep(kp, X, C0, G, 4, dense_switch=1.0)
+    assert all(s["path"] == kp.KM_PATH_FILTERED for s in st[1:])
+
+
+def test_final_assignment_stats(kp):
+    """kmeans_get_stats(-1): the record of the last fit's final assignment."""
+    w = synth.small_blobs(N=5000, D=16, K=12, G=3, seed=7)
+    km = kp.KMeans(dev(w.X), dev(w.C0), w.G)
+    with pytest.raises(kp.KMeansError) as e:
+        km.final_stats()
+    assert e.value.status == kp.KM_ESTATE
+    r = km.fit(30, 1e-4)
+    f = km.final_stats()
+    assert f["iter"] == r.n_iter and f["done"] == 1
+    assert f["path"] in (kp.KM_PATH_FILTERED, kp.KM_PATH_DENSE_FP32, kp.KM_PATH_DENSE_TC)
+    assert abs(f["objective"] - r.objective) <= 1e-12 * r.objective
+    km.reset(dev(w.C0))
+    with pytest.raises(kp.KMeansError):
+        km.final_stats()
+    km.close()
