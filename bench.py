@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run only the profiled pass (every kernel launched eagerly, timed with CUDA "
+                         "events) and print its breakdown: the command the ncu launch list is taken on")
     ap.add_argument("--n", type=int, default=1 << 20, help="points (default: the full workload)")
     return ap.parse_args()
 
@@ -279,6 +282,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profiled_pass(kpynq, X, C0, w, lab, C, stream, flush, steps):
+    """Fits launched kernel by kernel with CUDA events around every launch.
+    Returns per-kind (launches, ms), the launches that did work, and the
+    last fit's per-iteration statistics."""
+    prof = kpynq.KMeans(X, C0, w.G, stream=stream, profile=True)
+    pstats = None
+    kinds = {}
+    # launches that did work: the dense pass and its settle run only in dense
+    # iterations, the survivor kernel only in filtered ones (the others exit
+    # at once); every launch of the other kinds works
+    working = {"dense_assign": 0, "settle": 0, "survivor": 0}
+    for _ in range(steps):
+        flush.zero_()
+        prof.reset(C0)
+        r = prof.fit(w.max_iter, w.tol, lab, C)
+        pstats = r.stats
+        paths = [s["path"] for s in r.stats] + [prof.final_stats()["path"]]
+        nd = sum(1 for pa in paths if pa != kpynq.KM_PATH_FILTERED)
+        working["dense_assign"] += nd
+        working["settle"] += nd
+        working["survivor"] += len(paths) - nd
+        for k, (n, t) in prof.profile().items():
+            a = kinds.setdefault(k, [0, 0.0])
+            a[0] += n
+            a[1] += t
+    prof.close()
+    return kinds, working, pstats
+
+
+def breakdown_of(kinds, working):
+    total = sum(t for _, t in kinds.values())
+    out = {}
+    for k, (n, t) in kinds.items():
+        if not n:
+            continue
+        nw = working.get(k, n)
+        out[k] = {"launches": n, "working_launches": nw, "ms_total": round(t, 4),
+                  "share": round(t / total, 4) if total else None,
+                  "us_per_working_launch": round(1e3 * t / nw, 3) if nw else None}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -321,6 +366,13 @@ def run_ours(args):
         log(f"[{label}] {steps} steps: {statistics.mean(times):.3f} ms/step, iters {iters[0]}")
         return times, iters, kern, stats
 
+    if args.profile_only:
+        kinds, working, _ = profiled_pass(kpynq, X, C0, w, lab, C, stream, flush, args.profile_steps)
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "config": {"workload": w.name}, "fits": args.profile_steps,
+                              "kernel_breakdown": breakdown_of(kinds, working)}), flush=True)
+        return
+
     # --- the filtered method (the measured line) ---
     km = kpynq.KMeans(X, C0, w.G, stream=stream)
     torch.cuda.synchronize()
@@ -349,38 +401,9 @@ def run_ours(args):
     lloyd32.close()
 
     # --- profiled pass: CUDA events around every launch ---
-    prof = kpynq.KMeans(X, C0, w.G, stream=stream, profile=True)
-    pstats = None
-    kinds = {}
-    # launches that did work: the dense pass and its settle run only in dense
-    # iterations, the survivor kernel only in filtered ones (the others exit
-    # at once); every launch of the other kinds works
-    working = {"dense_assign": 0, "settle": 0, "survivor": 0}
-    for _ in range(args.profile_steps):
-        flush.zero_()
-        prof.reset(C0)
-        r = prof.fit(w.max_iter, w.tol, lab, C)
-        pstats = r.stats
-        paths = [s["path"] for s in r.stats] + [prof.final_stats()["path"]]
-        nd = sum(1 for pa in paths if pa != kpynq.KM_PATH_FILTERED)
-        working["dense_assign"] += nd
-        working["settle"] += nd
-        working["survivor"] += len(paths) - nd
-        for k, (n, t) in prof.profile().items():
-            a = kinds.setdefault(k, [0, 0.0])
-            a[0] += n
-            a[1] += t
-    prof.close()
+    kinds, working, pstats = profiled_pass(kpynq, X, C0, w, lab, C, stream, flush, args.profile_steps)
     hbm_peak, tc_peak, peak_src = measured_peaks()
-    total = sum(t for _, t in kinds.values())
-    breakdown = {}
-    for k, (n, t) in kinds.items():
-        if not n:
-            continue
-        nw = working.get(k, n)
-        breakdown[k] = {"launches": n, "working_launches": nw, "ms_total": round(t, 4),
-                        "share": round(t / total, 4) if total else None,
-                        "us_per_working_launch": round(1e3 * t / nw, 3) if nw else None}
+    breakdown = breakdown_of(kinds, working)
     dom = max(breakdown, key=lambda k: breakdown[k]["ms_total"])
     t_l = kinds[dom][1]
     n_l = working.get(dom, kinds[dom][0])
