@@ -52,6 +52,7 @@ struct Ctrl {
     uint32_t filter_ticket;  // last-block-done counter of the filter kernel
     unsigned long long kernels;  // kernels of this context run on the device
     int32_t settle_count;  // rows queued for the exact settle by the tensor-core pass
+    int32_t surv_next;     // next queue entry to hand out in the survivor kernel
     int32_t stats_full;    // the cluster sums of this iteration are recomputed in full
     uint32_t stats_ticket; // last-block-done counter of k_stats_hist
 };

@@ -199,8 +199,15 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
     unsigned long long c_scanned = 0, c_dist = 0, c_recheck = 0, c_changed = 0;
     const int lane = threadIdx.x & 31;
 
-    for (int64_t it = (int64_t)blockIdx.x * kTpThreads + threadIdx.x; it - lane < count;
-         it += (int64_t)gridDim.x * kTpThreads) {
+    // dynamic schedule: each warp takes the next 32 queue entries from a
+    // global counter (points differ a lot in work; a static split leaves
+    // SMs idle at the end)
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ctrl->surv_next, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= count) break;
+        const int64_t it = (int64_t)base + lane;
         const bool active = it < count;
         bool moved = false;
         int64_t n = 0;
