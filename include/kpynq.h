@@ -134,7 +134,7 @@ typedef struct {
     int32_t iter;          /* t */
     int32_t done;          /* the stop rule held after this iteration */
     int32_t path;          /* KM_PATH_*: how the assignment was computed */
-    int32_t reserved;
+    int32_t n_settle;      /* rows the tensor-core pass left to the exact settle */
     int64_t n_changed;     /* labels that changed (N at t = 0) */
     int64_t n_survivors;   /* points not kept by the global filter */
     int64_t n_scanned;     /* points still unresolved after tightening u */

@@ -187,6 +187,10 @@ int sync_and_check(kmeans_ctx *c) {
     KP_CUDA(c, cudaMemcpy(c->ctrl_host, c->p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
     c->t_host = c->ctrl_host->t;
     c->v_host = c->ctrl_host->v;
+    if (c->ctrl_host->err == kErrLabel)
+        return set_err(c, KM_ECUDA, "an assignment pass left a label outside [0, K)");
+    if (c->ctrl_host->err == kErrQueue)
+        return set_err(c, KM_ECUDA, "a work queue held an entry out of range");
     if (c->ctrl_host->err)
         return set_err(c, KM_ETIMEOUT, "a bounded device-side wait gave up (code %d)", c->ctrl_host->err);
     return KM_OK;

@@ -57,6 +57,10 @@ struct Ctrl {
     uint32_t stats_ticket; // last-block-done counter of k_stats_hist
 };
 
+// Device-side error codes in Ctrl::err (0 = none).
+constexpr int32_t kErrLabel = 0x4c41;  // an assignment left a label outside [0, K)
+constexpr int32_t kErrQueue = 0x5155;  // a work queue held a count or an entry out of range
+
 // every kernel of a context counts itself once (block 0, thread 0)
 __device__ __forceinline__ void count_kernel(Ctrl *c) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c->kernels, 1ull);
@@ -265,6 +269,17 @@ __device__ inline bool stage_to_smem(void *dst, const void *src, uint32_t bytes,
 __device__ __forceinline__ uint32_t stamp_u(uint32_t s) { return s >> 16; }
 __device__ __forceinline__ uint32_t stamp_l(uint32_t s) { return s & 0xffffu; }
 __device__ __forceinline__ uint32_t make_stamp(uint32_t vu, uint32_t vl) { return (vu << 16) | vl; }
+
+// A label read back from the label array; outside [0, K) (which no kernel
+// writes) records kErrLabel and returns -1 so that the caller skips the point.
+__device__ __forceinline__ int checked_label(const Params &p, int64_t n) {
+    const int k = p.label[n];
+    if ((unsigned)k >= (unsigned)p.K) {
+        atomicExch(&p.ctrl->err, kErrLabel);
+        return -1;
+    }
+    return k;
+}
 
 // drift of centroid k between versions w and v (upper bound)
 __device__ __forceinline__ float drift_c(const Params &p, int v, int w, int k) {

@@ -317,7 +317,8 @@ __global__ void __launch_bounds__(256) k_apply_moves(Params p, int all_points, i
         int old;
         if (all_points) { n = it; old = -1; }
         else { n = p.moved[it]; old = p.moved_old[it]; }
-        const int nw = p.label[n];
+        const int nw = checked_label(p, n);
+        if (nw < 0) continue;  // warp-uniform: one point per warp
         const float *x = p.X + n * p.D;
         // ||x||^2 as an FP32 pair (exact squares, compensated sum): FP64
         // arithmetic is slow on these SMs; only the atomics are FP64

@@ -535,7 +535,11 @@ __global__ void __launch_bounds__(kSettleThreads) k_settle(Params p, int first, 
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
-    const int count = *(volatile int *)&ctrl->settle_count;
+    int count = *(volatile int *)&ctrl->settle_count;
+    if (count < 0 || (int64_t)count > p.N) {  // cannot happen: at most one entry per row
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctrl->err, kErrQueue);
+        count = 0;
+    }
     const int warp_in = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (kSettleThreads / 32) + warp_in;
     const int64_t nwarps = (int64_t)gridDim.x * (kSettleThreads / 32);
@@ -552,6 +556,10 @@ __global__ void __launch_bounds__(kSettleThreads) k_settle(Params p, int first, 
     for (int64_t it = warp; it < count; it += nwarps) {
         const SettleReq q = p.sreq[it];
         const int64_t n = q.n;
+        if (n < 0 || n >= p.N || (unsigned)q.i1 >= (unsigned)K) {  // warp-uniform
+            if (lane == 0) atomicExch(&ctrl->err, kErrQueue);
+            continue;
+        }
         for (int i = lane; i < D / 4; i += 32)
             reinterpret_cast<float4 *>(xs)[i] = __ldg(reinterpret_cast<const float4 *>(p.X + n * D) + i);
         __syncwarp();

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_hist(Params p, int all_
         __syncthreads();
     }
     for (int64_t n = tid; n < p.N; n += nthr) {
-        const int k = p.label[n];
+        const int k = checked_label(p, n);
+        if (k < 0) continue;
         if (local) atomicAdd(&hist[k], 1);
         else atomicAdd(&p.hcount[k], 1);
     }
@@ -102,7 +103,8 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_scatter(Params p, int r
     if (!local) {  // large K: one global atomic per point
         for (int64_t n = (int64_t)blockIdx.x * kStatsThreads + threadIdx.x; n < p.N;
              n += (int64_t)gridDim.x * kStatsThreads) {
-            const int k = p.label[n];
+            const int k = checked_label(p, n);
+            if (k < 0) continue;
             const int pos = atomicAdd(&p.hcur[k], 1);
             p.perm[pos] = (int32_t)n;
             p.slab[pos] = k;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_scatter(Params p, int r
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t n = t0 + j * kStatsThreads + threadIdx.x;
-            k[j] = n < p.N ? p.label[n] : -1;
+            k[j] = n < p.N ? checked_label(p, n) : -1;
             if (k[j] >= 0) atomicAdd(&cnt[k[j]], 1);
         }
         __syncthreads();

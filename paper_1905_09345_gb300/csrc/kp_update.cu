@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         st.n_dist = (int64_t)ctrl->n_dist;
         st.n_recheck = (int64_t)ctrl->n_recheck;
         st.path = ctrl->path;
+        st.n_settle = ctrl->settle_count;
         st.objective = J;
         if (final_only) {
             ctrl->jfinal = J;

@@ -41,7 +41,7 @@ class kmeans_options(ctypes.Structure):
 
 class kmeans_iter_stats(ctypes.Structure):
     _fields_ = [("iter", ctypes.c_int32), ("done", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("n_changed", ctypes.c_int64),
+                ("n_settle", ctypes.c_int32), ("n_changed", ctypes.c_int64),
                 ("n_survivors", ctypes.c_int64), ("n_scanned", ctypes.c_int64), ("n_dist", ctypes.c_int64),
                 ("n_recheck", ctypes.c_int64), ("objective", ctypes.c_double), ("max_drift", ctypes.c_double)]
 
