@@ -276,6 +276,55 @@ KM_API int64_t kmeans_launch_count(void);
  * included, as of the end of the last blocking call. */
 KM_API int kmeans_get_kernel_count(const kmeans_ctx *ctx, int64_t *n);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent problems (uneven N, D, K) fitted by one
+ * CUDA graph launch.  Every problem keeps its own context (bounds, sums,
+ * loop control); the graph holds one chain per problem (arm -> iteration 0
+ * -> while(not done){ iteration } -> final assignment -> objective), so the
+ * problems run concurrently and each stops on its own rule.
+ * ------------------------------------------------------------------------ */
+typedef struct kmeans_batch kmeans_batch;
+
+typedef struct {
+    const float *X;               /* N x D row-major, host or device; a device X is borrowed */
+    int64_t N;
+    int32_t D, K, G;
+    const float *init_centroids;  /* K x D, host or device (copied at init) */
+} kmeans_problem;
+
+/* Create the contexts of n_problems problems with the options opt (NULL:
+ * defaults; profile must be 0; opt->stream is shared by all problems).
+ * tune_cache (nullable): path of the autotuner's cache.  When given, the
+ * dense/filtered switch of each size bucket (D, ceil log2 K, ceil log2 N) is
+ * taken from the file, or chosen by timing short fits of the bucket's
+ * largest problem with switches 0.5, 0.7, 0.9 and 1 (never) and written to
+ * it.  Errors: KM_EINVAL (bad arguments), the codes of kmeans_init. */
+KM_API int kmeans_batch_init(kmeans_batch **out, int32_t n_problems, const kmeans_problem *problems,
+                             const kmeans_options *opt, const char *tune_cache);
+
+/* Fit every problem (at most max_iter >= 1 iterations each, tol as kmeans_fit)
+ * with one graph launch; the graph is recorded on the first call and reused
+ * while max_iter, tol and the problems' state allow.  All problems must be
+ * fresh (after init or kmeans_batch_reset) or all continuing. */
+KM_API int kmeans_batch_fit(kmeans_batch *b, int32_t max_iter, double tol);
+
+/* Results of problem i: labels[N], centroids[K x D], objective, iterations
+ * run by the last fit (each nullable; host or device memory). */
+KM_API int kmeans_batch_get(kmeans_batch *b, int32_t i, int32_t *labels, float *centroids, double *objective,
+                            int32_t *n_iter);
+
+/* Restart every problem from its initial centroids (no allocation). */
+KM_API int kmeans_batch_reset(kmeans_batch *b);
+
+/* The dense/filtered switch the batch uses for problem i. */
+KM_API int kmeans_batch_get_switch(const kmeans_batch *b, int32_t i, float *dense_switch);
+
+KM_API void kmeans_batch_destroy(kmeans_batch *b);
+
+/* Message of the last failed batch call (b NULL: of the last failed
+ * kmeans_batch_init in this thread). */
+KM_API const char *kmeans_batch_last_error(const kmeans_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -351,6 +352,63 @@ int build_fit_graph_impl(kmeans_ctx *c) {
     c->graph = g;
     c->graph_exec = ex;
     c->cond = h;
+    return KM_OK;
+}
+
+// Append one problem's whole fit to graph g as an independent chain:
+// arm(max_iter, tol) -> [iteration 0] -> set_cond -> while(cond){ iteration }
+// -> final assignment -> objective.  Used by the batched form, which records
+// every problem's chain into one graph.
+int append_fit_chain(kmeans_ctx *c, cudaGraph_t g, int max_iter, double tol, bool first) {
+    c->capturing = true;
+    struct Off {
+        kmeans_ctx *c;
+        ~Off() { c->capturing = false; }
+    } off{c};
+    cudaGraphConditionalHandle h;
+    KP_CUDA(c, cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    Params p = c->p;
+    p.tcap = c->tcap;
+    Params pc = p;
+    pc.cond = (unsigned long long)h;
+
+    KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_arm(p, c->cap_stream, max_iter, tol);
+    if (e == cudaSuccess && first) e = enqueue_iteration(c, p, c->cap_stream, true, 1);
+    if (e == cudaSuccess) e = launch_set_cond(pc, c->cap_stream);
+    std::vector<cudaGraphNode_t> leaf;
+    if (e == cudaSuccess) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(c->cap_stream, &st, nullptr, nullptr, &deps, nullptr, &nd);
+        if (e == cudaSuccess) leaf.assign(deps, deps + nd);
+    }
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g2);
+    KP_CUDA(c, e);
+    KP_CUDA(c, e2);
+    if (leaf.empty()) return set_err(c, KM_ECUDA, "empty chain prologue");
+
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond_node;
+    KP_CUDA(c, cudaGraphAddNode(&cond_node, g, leaf.data(), nullptr, leaf.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    e = enqueue_iteration(c, pc, c->cap_stream, false, 1);
+    e2 = cudaStreamEndCapture(c->cap_stream, &body);
+    KP_CUDA(c, e);
+    KP_CUDA(c, e2);
+
+    KP_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, g, &cond_node, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    e = enqueue_assign(c, p, c->cap_stream, p.algo == KM_ALGO_LLOYD, false, 0);
+    if (e == cudaSuccess) e = enqueue_update(c, p, c->cap_stream, 1, 0);
+    e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    KP_CUDA(c, e);
+    KP_CUDA(c, e2);
     return KM_OK;
 }
 
@@ -742,5 +800,273 @@ KM_API void kmeans_destroy(kmeans_ctx *c) {
 KM_API const char *kmeans_last_error(const kmeans_ctx *c) { return c ? c->err : g_init_error; }
 
 KM_API int64_t kmeans_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent problems in one CUDA graph
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct kmeans_batch {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<kmeans_ctx *> ctx;
+    std::vector<float *> c0;         // device copies of the initial centroids
+    std::vector<float> sw;           // dense switch chosen per problem
+    cudaGraph_t graph = nullptr;     // every problem's fit, recorded once
+    cudaGraphExec_t exec = nullptr;
+    int rec_max_iter = -1;
+    double rec_tol = -1.0;
+    bool rec_first = false;
+    std::vector<int> rec_tcap;
+    char err[512] = "";
+};
+
+namespace {
+
+int batch_err(kmeans_batch *b, int code, const char *fmt, ...) {
+    char *buf = b ? b->err : g_init_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    if (b) set_thread_error(buf);
+    return code;
+}
+
+// ---- autotuner: the dense/filtered switch per size bucket ----------------
+// A bucket is (D, ceil log2 K, ceil log2 N).  For every bucket of the batch
+// the tuner runs a short fit (10 iterations) of the bucket's largest problem
+// once per candidate switch and keeps the fastest in points x iterations per
+// second; the choices are cached in a text file, one "D logK logN switch"
+// line per bucket, and read back on later runs.
+struct TuneKey {
+    int D, lk, ln;
+    bool operator<(const TuneKey &o) const {
+        return D != o.D ? D < o.D : (lk != o.lk ? lk < o.lk : ln < o.ln);
+    }
+};
+int ceil_log2(int64_t v) {
+    int l = 0;
+    while (((int64_t)1 << l) < v) ++l;
+    return l;
+}
+const float kTuneCandidates[] = {0.5f, 0.7f, 0.9f, 1.0f};
+
+float tune_one(const kmeans_problem &pr, const kmeans_options &base, cudaStream_t s) {
+    float best_sw = 0.0f;
+    double best_rate = -1.0;
+    for (float sw : kTuneCandidates) {
+        kmeans_options o = base;
+        o.dense_switch = sw;
+        o.stream = s;
+        o.profile = 0;
+        kmeans_ctx *c = nullptr;
+        if (kmeans_init(&c, static_cast<const float *>(pr.X), pr.N, pr.D, pr.K, pr.G, pr.init_centroids, &o) != KM_OK)
+            return 0.0f;
+        int32_t n_it = 0;
+        kmeans_fit(c, 2, 0.0, nullptr, nullptr, nullptr, &n_it);  // warm-up: records the graph
+        kmeans_reset(c, pr.init_centroids);
+        cudaEvent_t a, z;
+        cudaEventCreate(&a);
+        cudaEventCreate(&z);
+        cudaEventRecord(a, s);
+        const int rc = kmeans_fit(c, 10, 0.0, nullptr, nullptr, nullptr, &n_it);
+        cudaEventRecord(z, s);
+        cudaEventSynchronize(z);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, z);
+        cudaEventDestroy(a);
+        cudaEventDestroy(z);
+        kmeans_destroy(c);
+        if (rc != KM_OK || ms <= 0.f) continue;
+        const double rate = (double)pr.N * (n_it + 1) / ms;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best_sw = sw;
+        }
+    }
+    return best_sw;
+}
+
+void tune_batch(const kmeans_problem *probs, int n, const kmeans_options &base, const char *cache, cudaStream_t s,
+                std::vector<float> &sw) {
+    std::map<TuneKey, float> table;
+    if (FILE *f = fopen(cache, "r")) {
+        int D, lk, ln;
+        float v;
+        while (fscanf(f, "%d %d %d %f", &D, &lk, &ln, &v) == 4) table[{D, lk, ln}] = v;
+        fclose(f);
+    }
+    std::map<TuneKey, int> rep;  // the bucket's largest problem
+    for (int i = 0; i < n; ++i) {
+        const TuneKey k{probs[i].D, ceil_log2(probs[i].K), ceil_log2(probs[i].N)};
+        auto it = rep.find(k);
+        if (it == rep.end() || probs[i].N > probs[it->second].N) rep[k] = i;
+    }
+    bool grew = false;
+    for (auto &kv : rep) {
+        if (table.count(kv.first)) continue;
+        table[kv.first] = tune_one(probs[kv.second], base, s);
+        grew = true;
+    }
+    if (grew) {
+        if (FILE *f = fopen(cache, "w")) {
+            for (auto &kv : table) fprintf(f, "%d %d %d %.3f\n", kv.first.D, kv.first.lk, kv.first.ln, kv.second);
+            fclose(f);
+        }
+    }
+    sw.resize(n);
+    for (int i = 0; i < n; ++i) sw[i] = table[{probs[i].D, ceil_log2(probs[i].K), ceil_log2(probs[i].N)}];
+}
+
+int batch_record(kmeans_batch *b, int max_iter, double tol, bool first) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    if (e != cudaSuccess) return batch_err(b, KM_ECUDA, "cudaGraphCreate: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        int rc = append_fit_chain(b->ctx[i], b->graph, max_iter, tol, first);
+        if (rc) return batch_err(b, rc, "problem %zu: %s", i, b->ctx[i]->err);
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return batch_err(b, KM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    b->rec_max_iter = max_iter;
+    b->rec_tol = tol;
+    b->rec_first = first;
+    b->rec_tcap.resize(b->ctx.size());
+    for (size_t i = 0; i < b->ctx.size(); ++i) b->rec_tcap[i] = b->ctx[i]->tcap;
+    return KM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+KM_API int kmeans_batch_init(kmeans_batch **out, int32_t n_problems, const kmeans_problem *problems,
+                             const kmeans_options *opt, const char *tune_cache) {
+    if (!out) return batch_err(nullptr, KM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_problems < 1 || !problems) return batch_err(nullptr, KM_EINVAL, "n_problems must be >= 1 with a problem array");
+    kmeans_options base;
+    if (opt) base = *opt;
+    else kmeans_default_options(&base);
+    if (base.profile) return batch_err(nullptr, KM_EINVAL, "profile is not supported in a batch");
+    kmeans_batch *b = new kmeans_batch;
+    cudaGetDevice(&b->dev);
+    b->stream = static_cast<cudaStream_t>(base.stream);
+    std::vector<float> sw(n_problems, base.dense_switch);
+    if (tune_cache && tune_cache[0]) tune_batch(problems, n_problems, base, tune_cache, b->stream, sw);
+    b->sw = sw;
+    for (int i = 0; i < n_problems; ++i) {
+        const kmeans_problem &pr = problems[i];
+        kmeans_options o = base;
+        o.dense_switch = sw[i];
+        kmeans_ctx *c = nullptr;
+        int rc = kmeans_init(&c, static_cast<const float *>(pr.X), pr.N, pr.D, pr.K, pr.G, pr.init_centroids, &o);
+        if (rc) {
+            batch_err(b, rc, "problem %d: %s", i, kmeans_last_error(nullptr));
+            int keep = rc;
+            char msg[512];
+            memcpy(msg, b->err, sizeof(msg));
+            kmeans_batch_destroy(b);
+            return batch_err(nullptr, keep, "%s", msg);
+        }
+        b->ctx.push_back(c);
+        float *d0 = nullptr;
+        cudaError_t e = cudaMalloc(&d0, (size_t)pr.K * pr.D * 4);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d0, pr.init_centroids, (size_t)pr.K * pr.D * 4, cudaMemcpyDefault, b->stream);
+        b->c0.push_back(d0);
+        if (e != cudaSuccess) {
+            kmeans_batch_destroy(b);
+            return batch_err(nullptr, KM_ECUDA, "problem %d: %s", i, cudaGetErrorString(e));
+        }
+    }
+    cudaStreamSynchronize(b->stream);
+    *out = b;
+    return KM_OK;
+}
+
+KM_API int kmeans_batch_fit(kmeans_batch *b, int32_t max_iter, double tol) {
+    if (!b) return KM_EINVAL;
+    if (max_iter < 1 || !(tol >= 0.0)) return batch_err(b, KM_EINVAL, "max_iter must be >= 1 and tol >= 0");
+    DeviceGuard dg(b->dev);
+    bool first = true, any_started = false;
+    for (kmeans_ctx *c : b->ctx) {
+        if (c->broken) return batch_err(b, KM_ESTATE, "a problem's context is unusable");
+        first = first && c->t_host == 0;
+        any_started = any_started || c->t_host > 0;
+        int rc = ensure_tables(c, max_iter + 2);
+        if (rc) return batch_err(b, rc, "%s", c->err);
+    }
+    if (any_started && first == false) {
+        for (kmeans_ctx *c : b->ctx)
+            if (c->t_host == 0) return batch_err(b, KM_ESTATE, "problems at different iterations: reset the batch");
+    }
+    bool same = b->exec && b->rec_max_iter == max_iter && b->rec_tol == tol && b->rec_first == first;
+    for (size_t i = 0; same && i < b->ctx.size(); ++i) same = b->rec_tcap[i] == b->ctx[i]->tcap;
+    if (!same) {
+        int rc = batch_record(b, max_iter, tol, first);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return batch_err(b, KM_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        int rc = sync_and_check(b->ctx[i]);
+        if (rc) return batch_err(b, rc, "problem %zu: %s", i, b->ctx[i]->err);
+        b->ctx[i]->have_final = true;
+    }
+    return KM_OK;
+}
+
+KM_API int kmeans_batch_get(kmeans_batch *b, int32_t i, int32_t *labels, float *centroids, double *objective,
+                            int32_t *n_iter) {
+    if (!b) return KM_EINVAL;
+    if (i < 0 || i >= (int32_t)b->ctx.size()) return batch_err(b, KM_EINVAL, "problem %d out of range", i);
+    kmeans_ctx *c = b->ctx[i];
+    DeviceGuard dg(b->dev);
+    const Params &p = c->p;
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaSuccess;
+    if (labels) e = cudaMemcpyAsync(labels, p.label, (size_t)p.N * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess && centroids)
+        e = cudaMemcpy2DAsync(centroids, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K,
+                              cudaMemcpyDefault, s);
+    if (e == cudaSuccess && objective) e = cudaMemcpyAsync(objective, &p.ctrl->jfinal, 8, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return batch_err(b, KM_ECUDA, "%s", cudaGetErrorString(e));
+    if (n_iter) *n_iter = c->ctrl_host->fit_n_iter;
+    return KM_OK;
+}
+
+KM_API int kmeans_batch_reset(kmeans_batch *b) {
+    if (!b) return KM_EINVAL;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        int rc = kmeans_reset(b->ctx[i], b->c0[i]);
+        if (rc) return batch_err(b, rc, "problem %zu: %s", i, b->ctx[i]->err);
+    }
+    return KM_OK;
+}
+
+KM_API int kmeans_batch_get_switch(const kmeans_batch *b, int32_t i, float *dense_switch) {
+    if (!b || !dense_switch || i < 0 || i >= (int32_t)b->ctx.size()) return KM_EINVAL;
+    *dense_switch = b->sw[i];
+    return KM_OK;
+}
+
+KM_API void kmeans_batch_destroy(kmeans_batch *b) {
+    if (!b) return;
+    DeviceGuard dg(b->dev);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (kmeans_ctx *c : b->ctx) kmeans_destroy(c);
+    for (float *d : b->c0) cudaFree(d);
+    delete b;
+}
+
+KM_API const char *kmeans_batch_last_error(const kmeans_batch *b) { return b ? b->err : g_init_error; }
 
 }  // extern "C"

@@ -39,6 +39,11 @@ class kmeans_options(ctypes.Structure):
                 ("dense_switch", ctypes.c_float), ("reserved", ctypes.c_int64 * 5)]
 
 
+class kmeans_problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("D", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("G", ctypes.c_int32), ("init_centroids", ctypes.c_void_p)]
+
+
 class kmeans_iter_stats(ctypes.Structure):
     _fields_ = [("iter", ctypes.c_int32), ("done", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("n_settle", ctypes.c_int32), ("n_changed", ctypes.c_int64),
@@ -93,6 +98,21 @@ def lib():
         L.kmeans_last_error.restype = ctypes.c_char_p
         L.kmeans_launch_count.argtypes = []
         L.kmeans_launch_count.restype = i64
+        L.kmeans_batch_init.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(kmeans_problem),
+                                        ctypes.POINTER(kmeans_options), ctypes.c_char_p]
+        L.kmeans_batch_init.restype = ctypes.c_int
+        L.kmeans_batch_fit.argtypes = [vp, i32, dbl]
+        L.kmeans_batch_fit.restype = ctypes.c_int
+        L.kmeans_batch_get.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.kmeans_batch_get.restype = ctypes.c_int
+        L.kmeans_batch_reset.argtypes = [vp]
+        L.kmeans_batch_reset.restype = ctypes.c_int
+        L.kmeans_batch_get_switch.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
+        L.kmeans_batch_get_switch.restype = ctypes.c_int
+        L.kmeans_batch_destroy.argtypes = [vp]
+        L.kmeans_batch_destroy.restype = None
+        L.kmeans_batch_last_error.argtypes = [vp]
+        L.kmeans_batch_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -313,3 +333,97 @@ class KMeans:
     @property
     def kernel_count(self) -> int:
         return kmeans_get_kernel_count(self.ctx)
+
+
+def _check_batch(rc: int, b=None):
+    if rc != KM_OK:
+        msg = lib().kmeans_batch_last_error(b).decode(errors="replace")
+        raise KMeansError(rc, msg)
+
+
+def kmeans_batch_init(problems, opt: kmeans_options, tune_cache: str | None = None):
+    """problems: a ctypes array of kmeans_problem.  Returns the batch handle."""
+    b = ctypes.c_void_p()
+    _check_batch(lib().kmeans_batch_init(ctypes.byref(b), len(problems), problems, ctypes.byref(opt),
+                                         tune_cache.encode() if tune_cache else None))
+    return b
+
+
+def kmeans_batch_fit(b, max_iter: int, tol: float) -> None:
+    _check_batch(lib().kmeans_batch_fit(b, max_iter, tol), b)
+
+
+def kmeans_batch_get(b, i: int, labels=None, centroids=None):
+    """(objective, iterations of the last fit) of problem i."""
+    J = ctypes.c_double()
+    n = ctypes.c_int32()
+    _check_batch(lib().kmeans_batch_get(b, i, _addr(labels), _addr(centroids), ctypes.byref(J), ctypes.byref(n)), b)
+    return J.value, n.value
+
+
+def kmeans_batch_reset(b) -> None:
+    _check_batch(lib().kmeans_batch_reset(b), b)
+
+
+def kmeans_batch_get_switch(b, i: int) -> float:
+    v = ctypes.c_float()
+    _check_batch(lib().kmeans_batch_get_switch(b, i, ctypes.byref(v)), b)
+    return v.value
+
+
+def kmeans_batch_destroy(b) -> None:
+    lib().kmeans_batch_destroy(b)
+
+
+def kmeans_batch_last_error(b=None) -> str:
+    return lib().kmeans_batch_last_error(b).decode(errors="replace")
+
+
+class KMeansBatch:
+    """Many independent problems fitted by one CUDA graph launch.
+
+    ``problems``: a list of ``(X, C0, G)`` (N x D and K x D float32 arrays,
+    host or device; they must outlive the batch).  ``tune_cache``: path of
+    the autotuner's cache file (None: the library's default switch)."""
+
+    def __init__(self, problems, algo: int = KM_ALGO_FILTERED, stream=None, dense: int = KM_DENSE_AUTO,
+                 dense_switch: float = 0.0, tune_cache: str | None = None):
+        arr = (kmeans_problem * len(problems))()
+        self._keep = []
+        for i, (X, C0, G) in enumerate(problems):
+            N, D = X.shape
+            arr[i] = kmeans_problem(_addr(X), N, D, C0.shape[0], G, _addr(C0))
+            self._keep.append((X, C0))
+        self.shapes = [(X.shape[0], X.shape[1], C0.shape[0], G) for X, C0, G in problems]
+        opt = kmeans_options()
+        lib().kmeans_default_options(ctypes.byref(opt))
+        opt.algo = algo
+        opt.dense = dense
+        opt.dense_switch = dense_switch
+        if stream is not None:
+            opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self.b = kmeans_batch_init(arr, opt, tune_cache)
+
+    def fit(self, max_iter: int, tol: float = 0.0):
+        kmeans_batch_fit(self.b, max_iter, tol)
+
+    def reset(self):
+        kmeans_batch_reset(self.b)
+
+    def get(self, i: int, labels=None, centroids=None):
+        """(objective, iterations) of problem i; fills labels / centroids if given."""
+        return kmeans_batch_get(self.b, i, labels, centroids)
+
+    def switch(self, i: int) -> float:
+        return kmeans_batch_get_switch(self.b, i)
+
+    def close(self):
+        if getattr(self, "b", None):
+            kmeans_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
