@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "batched"],
+                    help="aniso1m: the 1M-point anisotropic job (default line); batched: 512 independent "
+                         "problems of uneven N, D, K fitted by one graph launch")
+    ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the profiled pass (every kernel launched eagerly, timed with CUDA "
                          "events) and print its breakdown: the command the ncu launch list is taken on")
@@ -482,10 +486,96 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """512 independent problems (N ~ logU[1e3, 2e5], D in {8,32,64,128},
+    K ~ logU[8,512], G = K/10, 25 iterations each) fitted by one graph launch
+    of the batched form, against the same problems fitted one after another
+    with single contexts.  Metric: points x iterations per second over the
+    batch."""
+    import tempfile
+    import torch
+    from paper_1905_09345_gb300 import kpynq, synth
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    specs = synth.batched_problems(args.problems, seed0=1000 * rank)
+    works = [synth.batched_problem(s) for s in specs]
+    dev = torch.device("cuda", local)
+    probs = [(torch.from_numpy(w.X).to(dev), torch.from_numpy(w.C0).to(dev), w.G) for w in works]
+    stream = torch.cuda.current_stream(dev)
+    max_iter = works[0].max_iter
+    cache = os.path.join(tempfile.gettempdir(), f"kpynq_tune_{os.getpid()}.txt")
+    t0 = time.perf_counter()
+    b = kpynq.KMeansBatch(probs, stream=stream, tune_cache=cache)
+    init_s = time.perf_counter() - t0
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_step():
+        flush.zero_()
+        b.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.fit(max_iter, 0.0)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        one_step()
+    with ClockSampler(gpu_uuid()) as clk:
+        times = [one_step() for _ in range(args.steps)]
+    iters = [b.get(i)[1] for i in range(len(works))]
+    units = sum(w.X.shape[0] * it for w, it in zip(works, iters))
+    ms = statistics.mean(times)
+    ms_max, units_all = aggregate(ms, units, ws_, dev)
+    value = units_all / (ms_max / 1e3)
+    switches = sorted(set(round(b.switch(i), 2) for i in range(len(works))))
+    b.close()
+    # the same problems, one fit after another (single contexts, graphs recorded beforehand)
+    kms = [kpynq.KMeans(X, C0, G, stream=stream) for X, C0, G in probs]
+    for km, (X, C0, G) in zip(kms, probs):
+        km.fit(max_iter, 0.0, with_stats=False)
+    seq = []
+    for _ in range(max(1, min(3, args.steps))):
+        for km, (X, C0, G) in zip(kms, probs):
+            km.reset(C0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for km in kms:
+            km.fit(max_iter, 0.0, with_stats=False)
+        torch.cuda.synchronize()
+        seq.append(time.perf_counter() - t1)
+    for km in kms:
+        km.close()
+    seq_value = units / statistics.mean(seq)
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
+    if rank != 0:
+        return
+    line = {
+        "metric": "points*iters/s (batched filtered K-means, 512 problems, exact labels)", "value": value,
+        "unit": UNIT, "n_gpus": ws_, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched{len(works)}", "problems": len(works),
+                   "points": int(sum(w.X.shape[0] for w in works)), "max_iter": max_iter,
+                   "step": "kmeans_batch_reset + kmeans_batch_fit (one graph launch)",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws_}"},
+        "clocks": clk.summary(),
+        "init_s": init_s, "tuned_switches": switches,
+        "sequential_single_contexts": {"value": seq_value, "s_per_step": statistics.mean(seq)},
+        "vs_sequential": value / seq_value,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 
