@@ -51,14 +51,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "batched"],
-                    help="aniso1m: the 1M-point anisotropic job (default line); batched: 512 independent "
-                         "problems of uneven N, D, K fitted by one graph launch")
+    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "highdim4m", "batched"],
+                    help="aniso1m: the 1M-point anisotropic job (default line); highdim4m: 4M points, "
+                         "D=128, K=1024, stored as bfloat16; batched: 512 independent problems of uneven "
+                         "N, D, K fitted by one graph launch")
     ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the profiled pass (every kernel launched eagerly, timed with CUDA "
                          "events) and print its breakdown: the command the ncu launch list is taken on")
-    ap.add_argument("--n", type=int, default=1 << 20, help="points (default: the full workload)")
+    ap.add_argument("--n", type=int, default=None, help="points (default: the full workload)")
     return ap.parse_args()
 
 
@@ -198,31 +199,37 @@ def oracle_iterations(Xs, C, iters: int) -> float:
 # ---------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic bytes / flops per launch of each kernel
 # ---------------------------------------------------------------------------
-def algorithmic(kind: str, w, stats: list, launches: int) -> tuple[str, float, str]:
-    """(bound, units per launch, unit) from the per-iteration counters."""
+def algorithmic(kind: str, w, stats: list, launches: int) -> list[tuple[str, float]]:
+    """[(bound, units per launch)] from the per-iteration counters: bytes for
+    "hbm", flops for "alu" (3 per point x centroid x dimension: the FSUB and
+    FFMA of a direct squared distance).  The caller keeps the bound with the
+    larger fraction of its peak."""
     N, D, K, G = w.N, w.D, w.K, w.G
     Gp = (G + 3) // 4 * 4
     filt = [s for s in stats if s["iter"] > 0]
+    dense_fp32 = [s for s in stats if s["path"] == 1]
+    mean = lambda key, rows: sum(s[key] for s in rows) / max(1, len(rows))
     if kind == "dense_assign":
         # X read once (FP32, or its two bfloat16 halves: 4 bytes per coordinate
         # either way) and label/u/lbg/stamp plus the lb row written per point
-        return "hbm", N * (4.0 * D + 16.0 + 4.0 * Gp), "byte"
+        out = [("hbm", N * (4.0 * D + 16.0 + 4.0 * Gp))]
+        if dense_fp32:  # the CUDA-core engine evaluates every distance
+            out.append(("alu", 3.0 * N * K * D))
+        return out
     if kind == "filter":
-        surv = sum(s["n_survivors"] for s in filt) / max(1, len(filt))
-        return "hbm", 16.0 * N + 4.0 * surv, "byte"
+        return [("hbm", 16.0 * N + 4.0 * mean("n_survivors", filt))]
     if kind == "survivor":
-        surv = sum(s["n_survivors"] for s in filt) / max(1, len(filt))
-        scan = sum(s["n_scanned"] for s in filt) / max(1, len(filt))
+        surv, scan = mean("n_survivors", filt), mean("n_scanned", filt)
         # per survivor: queue entry, label/stamp/lbg, x row, u/stamp writes;
         # per scanned point: lb row read + write, label/lbg/u/stamp writes
         b = surv * (4 + 12 + 4 * D + 8) + scan * (8 * Gp + 16)
-        return "hbm", b, "byte"
+        return [("hbm", b), ("alu", 3.0 * D * mean("n_dist", filt))]
     if kind == "apply_moves":
-        return "hbm", 4.0 * N * D + 4.0 * N, "byte"
+        return [("hbm", 4.0 * N * D + 4.0 * N)]
     if kind == "stats":
         # labels read twice, point ids and labels written and read once, X read once
-        return "hbm", 8.0 * N + 16.0 * N + 4.0 * N * D, "byte"
-    return "hbm", 0.0, "byte"
+        return [("hbm", 8.0 * N + 16.0 * N + 4.0 * N * D)]
+    return [("hbm", 0.0)]
 
 
 def source_sha(files) -> str:
@@ -243,16 +250,51 @@ KERNEL_SOURCES = {
 }
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, workload: str = "aniso1m"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel."""
+    on the current source of that kernel and on this workload."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d or d.get("source_sha") != source_sha(KERNEL_SOURCES.get(kernel, [])):
         return None
+    if d.get("workload", "aniso1m") != workload:
+        return None
     return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+# the oracle samples are sized to about the same FP64 work whatever K and D:
+# 2^18 points x K=256 x D=64 per timed iteration for the cpu_baseline
+ORACLE_WORK = (1 << 18) * 256 * 64
+
+
+def make_workload(args, rank: int = 0):
+    """The measured job (one replica per rank: the data seed follows the rank)."""
+    from paper_1905_09345_gb300 import synth
+    if args.workload == "highdim4m":
+        return synth.highdim_4m(N=args.n or 1 << 22, seed=3 + rank)
+    return synth.anisotropic_1m(N=args.n or 1 << 20, seed=2 + rank)
+
+
+def oracle_sample(w, work: int) -> int:
+    return max(1024, min(w.N, work // (w.K * w.D)))
+
+
+def device_points(w, dev, pinned: bool = False):
+    """X as the library is handed it: FP32, or bfloat16 bit patterns for the
+    workloads stored as bfloat16 (the library widens those exactly at init)."""
+    import numpy as np
+    import torch
+    from paper_1905_09345_gb300 import synth
+    if w.meta.get("storage") == "bf16":
+        t = torch.from_numpy(synth.bf16_bits(w.X).view(np.int16)).view(torch.bfloat16)
+    else:
+        t = torch.from_numpy(w.X)
+    return t.pin_memory() if pinned else t.to(dev)
 
 
 # ---------------------------------------------------------------------------
@@ -262,9 +304,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from paper_1905_09345_gb300 import synth
-    w = synth.anisotropic_1m(N=args.n)
-    n_sample = min(w.N, 1 << 16)
+    w = make_workload(args)
+    n_sample = oracle_sample(w, ORACLE_WORK // 4)
     import oracle
     oracle.build()
     Xs = w.X[:n_sample].astype("float64")
@@ -338,11 +379,11 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    from paper_1905_09345_gb300 import kpynq, synth
+    from paper_1905_09345_gb300 import kpynq
     kpynq.lib()
-    w = synth.anisotropic_1m(N=args.n, seed=2 + rank)  # one replica problem per rank
+    w = make_workload(args, rank)  # one replica problem per rank
     dev = torch.device("cuda", local)
-    X = torch.from_numpy(w.X).to(dev)
+    X = device_points(w, dev)
     C0 = torch.from_numpy(w.C0).to(dev)
     stream = torch.cuda.current_stream(dev)
     lab = torch.empty(w.N, dtype=torch.int32, device=dev)
@@ -396,13 +437,17 @@ def run_ours(args):
 
     # --- plain GPU Lloyd on the same GPU and inputs: tensor cores, FP32 ---
     lloyd = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream)
-    lt, li, _, _ = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd (BF16x3 tensor cores)")
+    lt, li, _, lst = timed_steps(lloyd, args.lloyd_steps, 1, "plain Lloyd (library default dense engine)")
     lloyd_value = w.N * statistics.mean(li) / (statistics.mean(lt) / 1e3)
     lloyd.close()
-    lloyd32 = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream, dense=kpynq.KM_DENSE_FP32)
-    lt32, li32, _, _ = timed_steps(lloyd32, args.lloyd_steps, 1, "plain Lloyd (FP32 CUDA cores)")
+    lloyd_tc = any(s["path"] == kpynq.KM_PATH_DENSE_TC for s in lst)
+    if lloyd_tc:
+        lloyd32 = kpynq.KMeans(X, C0, w.G, algo=kpynq.KM_ALGO_LLOYD, stream=stream, dense=kpynq.KM_DENSE_FP32)
+        lt32, li32, _, _ = timed_steps(lloyd32, args.lloyd_steps, 1, "plain Lloyd (FP32 CUDA cores)")
+        lloyd32.close()
+    else:  # the tensor-core engine does not take this shape: the default arm already is FP32
+        lt32, li32 = lt, li
     lloyd32_value = w.N * statistics.mean(li32) / (statistics.mean(lt32) / 1e3)
-    lloyd32.close()
 
     # --- profiled pass: CUDA events around every launch ---
     kinds, working, pstats = profiled_pass(kpynq, X, C0, w, lab, C, stream, flush, args.profile_steps)
@@ -411,24 +456,31 @@ def run_ours(args):
     dom = max(breakdown, key=lambda k: breakdown[k]["ms_total"])
     t_l = kinds[dom][1]
     n_l = working.get(dom, kinds[dom][0])
-    bound, units_l, uu = algorithmic(dom, w, pstats, n_l)
     per_launch_s = t_l / n_l / 1e3
-    if bound == "alu":
-        achieved = units_l / per_launch_s / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / ALU_PEAK_TFLOPS, "peak_source": "derived: 152 SMs x 128 FP32 lanes x "
-                "2.07 GHz x 1.5 flop/issue (FSUB+FFMA mix)"}
-    else:
-        achieved = units_l / per_launch_s / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} hbm_gbs"}
-    roof["traffic"] = ncu_traffic(dom)
+    roofs = []
+    for bound, units_l in algorithmic(dom, w, pstats, n_l):
+        if bound == "alu":
+            achieved = units_l / per_launch_s / 1e12
+            roofs.append({"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
+                          "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS, "_units": units_l,
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz x 1.5 flop/issue "
+                                         "(FSUB+FFMA mix)"})
+        else:
+            achieved = units_l / per_launch_s / 1e9
+            roofs.append({"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": achieved / hbm_peak, "_units": units_l, "peak_source": f"{peak_src} hbm_gbs"})
+    roof = max(roofs, key=lambda r: r["frac"])
+    units_l = roof.pop("_units")
+    if len(roofs) > 1:
+        other = [r for r in roofs if r is not roof][0]
+        roof["other_bound"] = {"bound": other["bound"], "frac": other["frac"]}
+    roof["traffic"] = ncu_traffic(dom, args.workload)
     roof["algorithmic_per_launch"] = units_l
     roof["launch_us"] = per_launch_s * 1e6
     roof["launches_averaged"] = n_l
 
     # --- end to end through the C ABI with host buffers ---
-    Xh = torch.from_numpy(w.X).pin_memory()
+    Xh = device_points(w, None, pinned=True)
     C0h = torch.from_numpy(w.C0).pin_memory()
     labh = torch.empty(w.N, dtype=torch.int32).pin_memory()
     Ch = torch.empty(w.K, w.D, dtype=torch.float32).pin_memory()
@@ -444,7 +496,8 @@ def run_ours(args):
             et.append(time.perf_counter() - t0)
             ei.append(r.n_iter)
     e2e_value = w.N * statistics.mean(ei) / statistics.mean(et)
-    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4 + C0h.numel() * 4),
+    e2e = {"value": e2e_value, "unit": UNIT,
+           "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + C0h.numel() * 4),
            "d2h_bytes_per_step": int(labh.numel() * 4 + Ch.numel() * 4 + 8 + 4),
            "ms_per_step": 1e3 * statistics.mean(et),
            "includes": "context creation (allocation, H2D copy of X), graph recording, fit, D2H of outputs"}
@@ -454,7 +507,7 @@ def run_ours(args):
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, min(w.N, 1 << 18), 3)
+        cpu = cpu_baseline(w, oracle_sample(w, ORACLE_WORK), 3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -462,7 +515,8 @@ def run_ours(args):
         "config": {"workload": w.name, "N": w.N, "D": w.D, "K": w.K, "G": w.G, "max_iter": w.max_iter,
                    "tol": w.tol, "iters_per_step": statistics.mean(iters),
                    "step": "kmeans_reset + kmeans_fit (dense iteration 0, filtered iterations, final assignment)",
-                   "l2": "flushed between steps (256 MiB write); X is 256 MiB > L2",
+                   "storage": w.meta.get("storage", "f32"),
+                   "l2": f"flushed between steps (256 MiB write); X is {w.N * w.D * 4 >> 20} MiB > L2",
                    "parallelism": f"replicas x{ws}"},
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -471,7 +525,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "skip_fraction": skip,
         "plain_lloyd": {"value": lloyd_value, "ms_per_step": statistics.mean(lt), "iters": statistics.mean(li),
-                        "dense": "BF16x3 tensor cores (tcgen05) + exact FP32/FP64 settle"},
+                        "dense": "BF16x3 tensor cores (tcgen05) + exact FP32/FP64 settle" if lloyd_tc else
+                                 "FP32 CUDA cores (the tensor-core engine does not take this shape)"},
         "vs_plain_lloyd": value / lloyd_value,
         "plain_lloyd_fp32": {"value": lloyd32_value, "ms_per_step": statistics.mean(lt32),
                              "iters": statistics.mean(li32), "dense": "FP32 CUDA cores"},

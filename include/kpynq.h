@@ -81,6 +81,15 @@ enum {
     KM_GROUP_CONTIGUOUS = 0 /* centroid j -> group floor(j * G / K) */
 };
 
+/* kmeans_options.dtype: storage type of X.  init_centroids and every output
+ * stay FP32; bfloat16 points are converted exactly to an FP32 copy made at
+ * init (so the tensor-core split of X has a zero low half and the oracle's
+ * FP64 values are the same numbers). */
+enum {
+    KM_DTYPE_F32 = 0,  /* X is N x D float */
+    KM_DTYPE_BF16 = 1  /* X is N x D bfloat16 (uint16 bit patterns) */
+};
+
 typedef struct {
     int32_t algo;        /* KM_ALGO_* */
     int32_t grouping;    /* KM_GROUP_* */
@@ -95,7 +104,9 @@ typedef struct {
                             instead (which also makes every bound exact again);
                             0 = library default (0.7 with the tensor-core
                             engine, 0.9 without), >= 1 = never */
-    int64_t reserved[5]; /* must be zero */
+    int32_t dtype;       /* KM_DTYPE_*: storage type of X */
+    int32_t pad0;        /* must be zero */
+    int64_t reserved[4]; /* must be zero */
 } kmeans_options;
 
 /* kmeans_options.dense: how dense passes (iteration 0, plain Lloyd) compute
@@ -324,6 +335,18 @@ KM_API void kmeans_batch_destroy(kmeans_batch *b);
 /* Message of the last failed batch call (b NULL: of the last failed
  * kmeans_batch_init in this thread). */
 KM_API const char *kmeans_batch_last_error(const kmeans_batch *b);
+
+/* Device self-test of the square-root bounds behind every distance bound
+ * (the upper bound u and the lower bounds lb of the filters, Sec. I): the
+ * library bounds sqrt(v) by the hardware approximation (sqrt.approx.f32)
+ * moved two steps of the bit pattern down / up, which is valid when the
+ * approximation is within one step of the correctly rounded root.  This
+ * checks lo >= 0 and lo^2 <= v <= hi^2 (squares in FP64, exact) for all 2^31
+ * non-negative float bit patterns v on the current device, synchronously
+ * (a few milliseconds), and writes the number of failures (0 expected) to
+ * *violations.  Allocates 8 bytes of device memory for the duration.  Errors:
+ * KM_EINVAL (NULL), KM_ENOMEM, KM_ECUDA; message in kmeans_last_error(NULL). */
+KM_API int kmeans_selftest_sqrt(int64_t *violations);
 
 #ifdef __cplusplus
 }

@@ -445,7 +445,9 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     if (o.grouping != KM_GROUP_CONTIGUOUS) return set_err(nullptr, KM_EINVAL, "unknown grouping %d", o.grouping);
     if (o.dense != KM_DENSE_AUTO && o.dense != KM_DENSE_FP32) return set_err(nullptr, KM_EINVAL, "unknown dense %d", o.dense);
     if (!(o.dense_switch >= 0.0f)) return set_err(nullptr, KM_EINVAL, "dense_switch must be >= 0");
-    for (int i = 0; i < 5; ++i)
+    if (o.dtype != KM_DTYPE_F32 && o.dtype != KM_DTYPE_BF16) return set_err(nullptr, KM_EINVAL, "unknown dtype %d", o.dtype);
+    if (o.pad0) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
+    for (int i = 0; i < 4; ++i)
         if (o.reserved[i]) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
 
     kmeans_ctx *c = new (std::nothrow) kmeans_ctx();
@@ -486,8 +488,21 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.algo = o.algo;
     const bool filtered = o.algo == KM_ALGO_FILTERED;
 
-    // X: borrowed when on the device, copied otherwise
-    if (is_device_ptr(X)) {
+    // X: borrowed when FP32 on the device, copied otherwise (bfloat16: an
+    // exact FP32 copy)
+    if (o.dtype == KM_DTYPE_BF16) {
+        INIT_CUDA(dalloc(c, &c->X_own, (size_t)N * D));
+        const uint16_t *xb = reinterpret_cast<const uint16_t *>(X);
+        uint16_t *tmp = nullptr;
+        if (!is_device_ptr(X)) {
+            INIT_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)N * D * 2, c->stream));
+            INIT_CUDA(cudaMemcpyAsync(tmp, X, (size_t)N * D * 2, cudaMemcpyDefault, c->stream));
+            xb = tmp;
+        }
+        INIT_CUDA(launch_bf16_to_f32(xb, (int64_t)N * D, c->X_own, c->stream, c->num_sms));
+        if (tmp) INIT_CUDA(cudaFreeAsync(tmp, c->stream));
+        p.X = c->X_own;
+    } else if (is_device_ptr(X)) {
         p.X = X;
     } else {
         INIT_CUDA(dalloc(c, &c->X_own, (size_t)N * D));
@@ -582,6 +597,13 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         SettleReq *sq;
         INIT_CUDA(dalloc(c, &sq, (size_t)N));
         p.sreq = sq;
+        uint32_t *sb;
+        int32_t *sqq;
+        INIT_CUDA(dalloc(c, &sb, (size_t)((N + 127) / 128) * 4));
+        INIT_CUDA(cudaMemsetAsync(sb, 0, (size_t)((N + 127) / 128) * 16, s));
+        INIT_CUDA(dalloc(c, &sqq, (size_t)N));
+        p.sbits = sb;
+        p.squeue = sqq;
     }
 
     if (o.validate) {

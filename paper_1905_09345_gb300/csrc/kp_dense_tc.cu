@@ -96,18 +96,6 @@ __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *m, int c0, 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Asynchronous TMEM read of 32 columns; the registers may be used only after
 // tmem_wait32 on the same array (which names them, so that the compiler
 // cannot move their uses above the wait).
@@ -164,22 +152,94 @@ __device__ __forceinline__ float row_norm2(const uint8_t *Ah, const uint8_t *Al,
     return a0 + a1;
 }
 
-// Stage the closing group's minimum and return the next boundary (a value
-// no column index reaches once the last group is open).
-__device__ __noinline__ int close_group(float *row, const int *gs, int &g, float gm1, int K) {
-    row[g] = gm1;
-    ++g;
-    const int e = gs[g + 1];
-    return e < K ? e : 0x7fffffff;
+// Running scan of one row over a run of accumulator columns: the per-group
+// minima (stored into the row's shared-memory slots as each group closes),
+// and the smallest value with its index and the runner-up, in two independent
+// chains (even and odd columns).  Branch-free: pen[c] is +inf where column c
+// opens a group (0 elsewhere), so that gm + pen restarts the running minimum,
+// and the closing minimum is stored by a predicated shared store.  A row is
+// scanned as two such runs (the two halves of its columns) interleaved column
+// by column, for instruction-level parallelism; merge() joins them.
+struct RowScan {
+    float b1[2], b2[2];
+    int i1[2];
+    float gm;     // minimum of the open group
+    uint32_t rp;  // shared-memory address of the open group's slot
+
+    __device__ __forceinline__ void init(const float *slot) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            b1[c] = INFINITY;
+            b2[c] = INFINITY;
+            i1[c] = 0;  // kept when no column is below +inf (then column 0)
+        }
+        gm = INFINITY;
+        rp = smem_u32(slot);
+    }
+    __device__ __forceinline__ void col(float acc, float cnv, float pen, int c, int jpar) {
+        const float t = fmaf(-2.f, acc, cnv);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.f32 p, %2, 0f00000000;\n\t@p st.shared.f32 [%0], %1;\n\t"
+            "@p add.u32 %0, %0, 4;\n\t}"
+            : "+r"(rp)
+            : "f"(gm), "f"(pen)
+            : "memory");
+        gm = fminf(__fadd_rn(gm, pen), t);
+        b2[jpar] = fminf(b2[jpar], fmaxf(b1[jpar], t));
+        const bool lt = t < b1[jpar];
+        b1[jpar] = lt ? t : b1[jpar];
+        i1[jpar] = lt ? c : i1[jpar];
+    }
+    // store the open group's minimum
+    __device__ __forceinline__ void close() const {
+        asm volatile("st.shared.f32 [%0], %1;" ::"r"(rp), "f"(gm) : "memory");
+    }
+    // winner (lowest index among equal values) and runner-up of both chains
+    __device__ __forceinline__ void result(float &w1, int &wi, float &w2) const {
+        const bool odd = b1[1] < b1[0] || (b1[1] == b1[0] && i1[1] < i1[0]);
+        w1 = odd ? b1[1] : b1[0];
+        wi = odd ? i1[1] : i1[0];
+        w2 = fminf(fminf(b2[0], b2[1]), fmaxf(b1[0], b1[1]));
+    }
+};
+
+// two runs of 32 columns each (chunks ca of run A and cb of run B), column by
+// column; cn / pen read four columns at a time
+__device__ __forceinline__ void scan_pair(RowScan &A, const uint32_t (&ra)[32], int ca, RowScan &B,
+                                          const uint32_t (&rb)[32], int cb, const float *cn, const float *pen) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 na = *reinterpret_cast<const float4 *>(cn + ca + j);
+        const float4 pa = *reinterpret_cast<const float4 *>(pen + ca + j);
+        const float4 nb = *reinterpret_cast<const float4 *>(cn + cb + j);
+        const float4 pb = *reinterpret_cast<const float4 *>(pen + cb + j);
+        const float nav[4] = {na.x, na.y, na.z, na.w}, pav[4] = {pa.x, pa.y, pa.z, pa.w};
+        const float nbv[4] = {nb.x, nb.y, nb.z, nb.w}, pbv[4] = {pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            A.col(__uint_as_float(ra[j + jj]), nav[jj], pav[jj], ca + j + jj, jj & 1);
+            B.col(__uint_as_float(rb[j + jj]), nbv[jj], pbv[jj], cb + j + jj, jj & 1);
+        }
+    }
+}
+__device__ __forceinline__ void scan_one(RowScan &A, const uint32_t (&ra)[32], int ca, const float *cn,
+                                         const float *pen) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 na = *reinterpret_cast<const float4 *>(cn + ca + j);
+        const float4 pa = *reinterpret_cast<const float4 *>(pen + ca + j);
+        const float nav[4] = {na.x, na.y, na.z, na.w}, pav[4] = {pa.x, pa.y, pa.z, pa.w};
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) A.col(__uint_as_float(ra[j + jj]), nav[jj], pav[jj], ca + j + jj, jj & 1);
+    }
 }
 
-__device__ __forceinline__ float sqrt_dn(float v) {  // <= sqrt(v)
-    const float q = __fsqrt_rn(fmaxf(v, 0.f));
-    return q > 0.f ? __int_as_float(__float_as_int(q) - 1) : 0.f;
-}
-__device__ __forceinline__ float sqrt_up(float v) {  // >= sqrt(v)
-    const float q = __fsqrt_rn(fmaxf(v, 0.f));
-    return __int_as_float(__float_as_int(q) + 1);
+// group of column `col` from the boundary masks (contiguous groups)
+__device__ __forceinline__ int group_of(const uint32_t *bm, int col) {
+    const int c = col >> 5;
+    int g = __popc(bm[c] & ((2u << (col & 31)) - 1u));
+    for (int i = 0; i < c; ++i) g += __popc(bm[i]);
+    return g;
 }
 
 template <int D>
@@ -199,8 +259,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint8_t *sBh = sm;
     uint8_t *sBl = sm + NA * b_atom;
     uint8_t *sA = sm + cfg.off_A;  // stage s: [NA atoms of x_h][NA atoms of x_l]
-    float *cn = reinterpret_cast<float *>(sm + cfg.off_cn);
-    int *gs = reinterpret_cast<int *>(sm + cfg.off_gs);
+    float *cn = reinterpret_cast<float *>(sm + cfg.off_cn);  // [Kp] ||c||^2 (+inf: padding)
+    float *pen = cn + Kp;  // [Kp] +inf where a group opens, else 0
+    uint32_t *bm = reinterpret_cast<uint32_t *>(sm + cfg.off_gs);  // [Kp / 32] group-start masks
     float *stage = reinterpret_cast<float *>(sm + cfg.off_stage);  // [8 warps x 32 rows][Gp + 1]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + cfg.off_bar);
     const int S = cfg.stages;
@@ -235,7 +296,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int g = threadIdx.x; g <= G; g += blockDim.x) gs[g] = p.gstart[g];
+    for (int c = threadIdx.x; c < Kp / 32; c += blockDim.x) bm[c] = 0u;
     // the centroid block, split into x_h / x_l bfloat16 tiles (128-byte swizzle),
     // and the exact FP32 norms (padding rows: zero tiles, norm +inf)
     for (int idx = threadIdx.x; idx < Kp * (D / 8); idx += blockDim.x) {
@@ -270,10 +331,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 cm = fmaxf(cm, s2);
             }
             cn[k] = s2;
+            pen[k] = 0.f;
         }
         cm = warp_max(cm);
-        __syncthreads();  // c2max_s initialised
+        __syncthreads();  // c2max_s and the masks initialised
         if (lane == 0 && cm > 0.f) atomicMax(reinterpret_cast<int *>(c2max_s), __float_as_int(cm));
+        // group g >= 1 starts at column gstart[g] (< K <= Kp)
+        for (int g = 1 + threadIdx.x; g < G; g += blockDim.x) {
+            const int col = p.gstart[g];
+            if ((unsigned)col < (unsigned)Kp) {
+                atomicOr(&bm[col >> 5], 1u << (col & 31));
+                pen[col] = INFINITY;
+            }
+        }
     }
     // generic-proxy writes of the B tiles must be visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -354,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int r = q * 32 + lane;
         const bool bounds = p.algo == KM_ALGO_FILTERED;
         const float c2max = __fmul_ru(*c2max_s, 1.0f + 1.0f / 1024);
-        const float cmax = sqrt_up(c2max);
+        const float cmax = sqrt_hi(c2max);
         const float ec2 = __fmul_ru(cfg.e_c2, c2max);
         float *row = stage + (size_t)((warp - 2) * 32 + lane) * (p.Gp + 1);
         unsigned long long c_changed = 0, c_recheck = 0, c_dist = 0;
@@ -370,43 +440,62 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
             const int64_t n = (int64_t)tile * kTM + r;
             const bool valid = n < p.N;
+            // the previous label, read now so that its latency hides behind the scan
+            const int old = valid ? (first ? -1 : p.label[n]) : -1;
             const float xn = row_norm2<D>(st, st + NA * kAtomBytes, r);
             // the split copy of A is no longer needed
             __syncwarp();
             if (lane == 0) bar_arrive(&empty_a[s]);
             const float xlo = __fmul_rd(xn, cfg.xn_lo), xup = __fmul_ru(xn, cfg.xn_hi);
-            const float E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_up(xup), cmax), ec2);
+            const float E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
             const float twoE = __fmul_ru(2.f, E);
             const uint32_t tb = tmem + (uint32_t)(grp_id * cfg.buf_cols) + ((uint32_t)(q * 32) << 16);
 
-            // pass 1: group minima (staged), winner (lowest index on ties), runner-up
-            float b1 = INFINITY, b2 = INFINITY, gm1 = INFINITY;
-            int i1 = 0, cur_g = 0, gend = gs[1] < K ? gs[1] : 0x7fffffff;
-            for (int c0 = 0; c0 < Kp; c0 += 32) {
-                uint32_t rr[32];
-                tmem_ld32(tb + c0, rr);
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    const float4 c4 = *reinterpret_cast<const float4 *>(cn + c0 + j);
-                    const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int col = c0 + j + jj;
-                        const float t = fmaf(-2.f, __uint_as_float(rr[j + jj]), cv[jj]);
-                        if (col == gend) {  // uniform
-                            gend = close_group(row, gs, cur_g, gm1, K);
-                            gm1 = INFINITY;
-                        }
-                        gm1 = fminf(gm1, t);
-                        b2 = fminf(b2, fmaxf(b1, t));
-                        if (t < b1) {
-                            b1 = t;
-                            i1 = col;
-                        }
+            // pass 1: group minima (staged), winner (lowest index on ties), runner-up;
+            // the next 32 columns are read from TMEM while the current ones are scanned
+            float b1, b2;
+            int i1;
+            {
+                // two runs: chunks [0, ha) and [ha, nch) of 32 columns
+                const int nch = Kp >> 5, ha = (nch + 1) >> 1;
+                RowScan A, B;
+                A.init(row);
+                // run B starts inside the group open at its first column's left
+                // neighbour; its first store lands in that group's slot, which
+                // is merged with run A's last minimum below
+                const int gsplit = nch > 1 ? group_of(bm, 32 * ha - 1) : 0;
+                B.init(row + gsplit);
+                uint32_t ra[32], rb[32];
+                for (int k = 0; k < ha; ++k) {
+                    const bool two = ha + k < nch;  // warp-uniform
+                    tmem_ld32_async(tb + 32 * k, ra);
+                    if (two) tmem_ld32_async(tb + 32 * (ha + k), rb);
+                    tmem_wait32(ra);
+                    if (two) {
+                        tmem_wait32(rb);
+                        scan_pair(A, ra, 32 * k, B, rb, 32 * (ha + k), cn, pen);
+                    } else {
+                        scan_one(A, ra, 32 * k, cn, pen);
                     }
                 }
+                if (nch > 1) {
+                    B.close();
+                    const float gmA = A.gm;
+                    asm volatile("" ::: "memory");
+                    row[gsplit] = fminf(row[gsplit], gmA);
+                } else {
+                    A.close();
+                }
+                float a1, a2, c1, c2;
+                int ai, ci;
+                A.result(a1, ai, a2);
+                B.result(c1, ci, c2);
+                // run A holds the lower indices: it wins ties
+                const bool bw = c1 < a1;
+                b1 = bw ? c1 : a1;
+                i1 = bw ? ci : ai;
+                b2 = fminf(fminf(a2, c2), fmaxf(a1, c1));
             }
-            row[cur_g] = gm1;
             const float thr = __fadd_ru(b1, twoE);
 
             // Rows whose runner-up is inside the error window go to the settle
@@ -416,7 +505,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // tensor-core winner i1, which is among them).  The epilogue writes such a
             // row's bounds as if the tensor-core winner i1 won; k_settle
             // corrects them when it does not.
-            const int old = valid ? (first ? -1 : p.label[n]) : -1;
             const bool need = valid && b2 <= thr;
             {
                 const unsigned nm = __ballot_sync(0xffffffffu, need);
@@ -428,21 +516,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         gmask = 0ull;
                         for (int g = 0; g < G; ++g) gmask |= (row[g] <= thr) ? (1ull << g) : 0ull;
                     }
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&ctrl->settle_count, __popc(nm));
-                    base = __shfl_sync(0xffffffffu, base, 0);
                     if (need) {
-                        SettleReq q;
-                        q.n = (int32_t)n;
-                        q.old = old;
-                        q.i1 = i1;
+                        SettleReq rq;
+                        rq.n = (int32_t)n;
+                        rq.old = old;
+                        rq.i1 = i1;
                         // every column is at least b1: when i1 loses, this bounds both
                         // i1's group (which now keeps i1) and the winner's group
-                        q.lb_alt = sqrt_dn(__fsub_rd(__fadd_rd(xlo, b1), E));
-                        q.gmask = gmask;
-                        p.sreq[base + __popc(nm & ((1u << lane) - 1u))] = q;
+                        rq.lb_alt = sqrt_lo(__fsub_rd(__fadd_rd(xlo, b1), E));
+                        rq.gmask = gmask;
+                        p.sreq[n] = rq;
                     }
                 }
+                // the warp's 32 rows in the request bitmap (every word is written
+                // by every dense pass, so the bitmap needs no clearing)
+                if (lane == 0) p.sbits[(int64_t)tile * (kTM / 32) + q] = nm;
             }
             // accumulators no longer needed
             tc_fence_before();
@@ -455,25 +543,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (!need) p.label[n] = best;
                 if (bounds) {
                     // s_c >= xn_lo + t_c - E for every column c
+#pragma unroll 4
                     for (int g = 0; g < G; ++g) {
                         const float tg = row[g];
-                        row[g] = tg == INFINITY ? INFINITY : sqrt_dn(__fsub_rd(__fadd_rd(xlo, tg), E));
+                        row[g] = tg == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, tg), E));
                     }
                     // the winner's group must exclude the winner: every other
                     // column is at least the runner-up b2 (at least b1 when the
                     // exact winner is not the tensor-core winner)
                     const float tw = best == i1 ? b2 : b1;
-                    row[p.grp[best]] = tw == INFINITY ? INFINITY : sqrt_dn(__fsub_rd(__fadd_rd(xlo, tw), E));
-                    float mm = INFINITY;
-                    for (int g = 0; g < G; ++g) mm = fminf(mm, row[g]);
-                    p.lbg[n] = mm;
-                    p.u[n] = sqrt_up(__fadd_ru(__fadd_ru(xup, b1), E));
+                    const float lw = tw == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, tw), E));
+                    row[group_of(bm, best)] = lw;
+                    // the bound is monotone in t, so the smallest group bound is
+                    // the bound of the smallest column other than the winner
+                    p.lbg[n] = lw;
+                    p.u[n] = sqrt_hi(__fadd_ru(__fadd_ru(xup, b1), E));
                     p.stamp[n] = make_stamp(v, v);
                 }
-                if (!need && old != best) {
-                    c_changed += 1;
-                    if (!first) {
-                        const int slot = atomicAdd(&ctrl->moved_count, 1);
+            }
+            {
+                // label changes: one slot reservation per warp
+                const bool moved = valid && !need && old != best;
+                const unsigned mm = __ballot_sync(0xffffffffu, moved);
+                c_changed += moved ? 1 : 0;
+                if (mm && !first) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&ctrl->moved_count, __popc(mm));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (moved) {
+                        const int slot = base + __popc(mm & ((1u << lane) - 1u));
                         p.moved[slot] = (int)n;
                         p.moved_old[slot] = old;
                     }
@@ -485,11 +583,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int64_t n0 = (int64_t)tile * kTM + q * 32;
                 const int rows = (int)min((int64_t)32, p.N - n0);
                 if (rows > 0) {
-                    const float *st0 = stage + (size_t)((warp - 2) * 32) * (p.Gp + 1);
-                    float *dst = p.lb + n0 * p.Gp;
-                    for (int rw = 0; rw < rows; ++rw)
-                        for (int g = lane; g < p.Gp; g += 32)
-                            dst[(size_t)rw * p.Gp + g] = g < G ? st0[rw * (p.Gp + 1) + g] : 0.f;
+                    // rows x Gp floats, contiguous in lb: 16-byte stores (Gp is a
+                    // multiple of 4, so no vector crosses a row)
+                    const int Gp = p.Gp, q4 = Gp >> 2;
+                    const float *st0 = stage + (size_t)((warp - 2) * 32) * (Gp + 1);
+                    float4 *dst = reinterpret_cast<float4 *>(p.lb + n0 * Gp);
+                    for (int e = lane; e < rows * q4; e += 32) {
+                        const int rw = e / q4, g = (e - rw * q4) * 4;
+                        const float *src = st0 + rw * (Gp + 1) + g;
+                        float4 v4;
+                        v4.x = g < G ? src[0] : 0.f;
+                        v4.y = g + 1 < G ? src[1] : 0.f;
+                        v4.z = g + 2 < G ? src[2] : 0.f;
+                        v4.w = g + 3 < G ? src[3] : 0.f;
+                        dst[e] = v4;
+                    }
                 }
                 __syncwarp();
             }
@@ -517,126 +625,206 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---------------------------------------------------------------------------
 // k_settle: the exact decision for the rows the tensor-core epilogue queued
-// (runner-up inside the error window).  One warp per row, lanes over the
-// candidate centroids (those of the groups whose tensor-core minimum lies in
-// the window; C staged in shared memory, the row in registers): the FP32
-// direct-difference distances, the smallest with the lowest index, and where
-// FP32 cannot separate it from the runner-up, FP64 with the summation order
-// of the FP64 definition among the unresolved ones.
-// Writes the label, corrects u / lb / lbg when the winner is not i1, and
-// appends label changes to the moved-point list.
+// (runner-up inside the error window).  One thread per request, so that the
+// requests' loads and arithmetic overlap across the warp: the row in
+// registers, the candidate centroids (those of the groups whose tensor-core
+// minimum lies in the window) from shared memory, FP32 direct-difference
+// distances, the smallest with the lowest index, and where FP32 cannot
+// separate it from the runner-up, FP64 with the summation order of the FP64
+// definition among the unresolved ones.  Threads walk the request bitmap one
+// 32-row word at a time.  Writes the label, corrects u / lb / lbg when the
+// winner is not i1, and appends label changes to the moved-point list.
 // ---------------------------------------------------------------------------
 constexpr int kSettleThreads = 256;
 
+// FP32 squared distance of the row (packed pairs in registers) to a centroid
+// row in shared memory: packed FP32x2 subtract / fused multiply-add (each
+// half an ordinary round-to-nearest FP32 operation; four partial sums)
 template <int D>
-__global__ void __launch_bounds__(kSettleThreads) k_settle(Params p, int first, int respect_done) {
-    extern __shared__ __align__(128) float sm_settle[];  // C (K x Dp) | per-warp row (D)
-    __shared__ __align__(8) uint64_t bar;
+__device__ __forceinline__ float settle_fp32(const ulonglong2 (&xr)[D / 4], const float *c) {
+    const ulonglong2 *c2p = reinterpret_cast<const ulonglong2 *>(c);
+    unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+    for (int i = 0; i < D / 4; ++i) {
+        const ulonglong2 c2 = c2p[i];
+        unsigned long long d0, d1;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(xr[i].x), "l"(c2.x));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(xr[i].y), "l"(c2.y));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
+    }
+    float l0, h0, l1, h1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(h0) : "l"(a0));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l1), "=f"(h1) : "l"(a1));
+    return (l0 + h0) + (l1 + h1);
+}
+// FP64 squared distance, i ascending, no fused multiply-add (the rare
+// near-tie path: the row is read again from global memory)
+__device__ __noinline__ double settle_fp64(const float *x, const float *c, int D) {
+    double s = 0.0;
+    for (int i = 0; i < D; ++i) {
+        const double t = __dsub_rn((double)__ldg(x + i), (double)c[i]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+// FP32 squared distance with the row read from global memory (rows too long
+// to keep in registers)
+template <int D>
+__device__ __forceinline__ float settle_fp32_g(const float *x, const float *c) {
+    const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(x);
+    const ulonglong2 *c2p = reinterpret_cast<const ulonglong2 *>(c);
+    unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll 8
+    for (int i = 0; i < D / 4; ++i) {
+        const ulonglong2 x2 = __ldg(xp + i), c2 = c2p[i];
+        unsigned long long d0, d1;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(x2.x), "l"(c2.x));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(x2.y), "l"(c2.y));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
+    }
+    float l0, h0, l1, h1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(h0) : "l"(a0));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l1), "=f"(h1) : "l"(a1));
+    return (l0 + h0) + (l1 + h1);
+}
+
+// The bitmap's set bits, compacted into the settle queue: a warp takes 32
+// words, scans their populations and reserves its slots with one atomic.
+__global__ void k_settle_gather(Params p, int respect_done) {
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
-    int count = *(volatile int *)&ctrl->settle_count;
-    if (count < 0 || (int64_t)count > p.N) {  // cannot happen: at most one entry per row
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctrl->err, kErrQueue);
-        count = 0;
+    if (*(volatile int *)&ctrl->path != KM_PATH_DENSE_TC) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwords = (p.N + 31) / 32;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < nwords; w0 += stride) {
+        const int64_t w = w0 + lane;
+        const uint32_t bits = w < nwords ? p.sbits[w] : 0u;
+        const int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&ctrl->settle_count, tot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        int64_t pos = (int64_t)base + incl - c;
+        for (uint32_t b = bits; b; b &= b - 1u) {
+            const int64_t n = w * 32 + (__ffs(b) - 1);
+            if (pos < p.N && n < p.N) p.squeue[pos] = (int32_t)n;
+            ++pos;
+        }
     }
-    const int warp_in = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (kSettleThreads / 32) + warp_in;
-    const int64_t nwarps = (int64_t)gridDim.x * (kSettleThreads / 32);
-    if ((int64_t)blockIdx.x * (kSettleThreads / 32) >= count) return;  // uniform per block
-    const int K = p.K;
-    if (!stage_to_smem(sm_settle, p.C, (uint32_t)((size_t)K * p.Dp * 4), &bar, ctrl)) return;
-    const float *Cs = sm_settle;
-    float *xs = sm_settle + (size_t)K * p.Dp + warp_in * D;
-    int32_t *gs_s = reinterpret_cast<int32_t *>(sm_settle + (size_t)K * p.Dp + (kSettleThreads / 32) * D);
-    for (int i = threadIdx.x; i <= p.G; i += kSettleThreads) gs_s[i] = p.gstart[i];
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSettleThreads, 2) k_settle(Params p, int first, int respect_done) {
+    extern __shared__ __align__(16) float sm_settle[];  // C (K rows, stride SD) | group starts
+    Ctrl *ctrl = p.ctrl;
+    count_kernel(ctrl);
+    if (respect_done && *(volatile int *)&ctrl->done) return;
+    // the requests of this iteration's dense pass, if it ran on the tensor cores
+    if (*(volatile int *)&ctrl->path != KM_PATH_DENSE_TC) return;
+    int64_t total = *(volatile int *)&ctrl->settle_count;
+    if (total < 0 || total > p.N) {  // cannot happen: at most one request per row
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctrl->err, kErrQueue);
+        total = 0;
+    }
+    const int64_t gt = (int64_t)blockIdx.x * kSettleThreads + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * kSettleThreads;
+    if ((int64_t)blockIdx.x * kSettleThreads >= total) return;  // uniform per block
+    const int K = p.K, G = p.G;
+    // C with a row stride of D + 4 floats: 16-byte reads of different rows by
+    // the threads of a warp spread over the banks
+    constexpr int SD = D + 4;
+    float *Cs = sm_settle;
+    int32_t *gs_s = reinterpret_cast<int32_t *>(sm_settle + (size_t)K * SD);
+    for (int i = threadIdx.x; i < K * (D / 4); i += kSettleThreads) {
+        const int row = i / (D / 4), q4 = i - row * (D / 4);
+        reinterpret_cast<float4 *>(Cs + (size_t)row * SD)[q4] =
+            __ldg(reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp) + q4);
+    }
+    for (int i = threadIdx.x; i <= G; i += kSettleThreads) gs_s[i] = p.gstart[i];
     __syncthreads();
     const bool bounds = p.algo == KM_ALGO_FILTERED;
     unsigned long long c_changed = 0, c_recheck = 0;
-    for (int64_t it = warp; it < count; it += nwarps) {
-        const SettleReq q = p.sreq[it];
-        const int64_t n = q.n;
-        if (n < 0 || n >= p.N || (unsigned)q.i1 >= (unsigned)K) {  // warp-uniform
-            if (lane == 0) atomicExch(&ctrl->err, kErrQueue);
-            continue;
-        }
-        for (int i = lane; i < D / 4; i += 32)
-            reinterpret_cast<float4 *>(xs)[i] = __ldg(reinterpret_cast<const float4 *>(p.X + n * D) + i);
-        __syncwarp();
-        // the row as packed FP32 pairs in registers; distances with packed
-        // FP32x2 subtract / fused multiply-add (each lane of a pair an ordinary
-        // round-to-nearest FP32 operation; four partial sums of D/4 terms)
-        ulonglong2 xr[D / 4];
+    for (int64_t r = gt; r < total; r += nthreads) {
+        {
+            const int64_t n = p.squeue[r];
+            if (n < 0 || n >= p.N) {
+                atomicExch(&ctrl->err, kErrQueue);
+                continue;
+            }
+            const SettleReq q = p.sreq[n];
+            if (q.n != n || (unsigned)q.i1 >= (unsigned)K) {
+                atomicExch(&ctrl->err, kErrQueue);
+                continue;
+            }
+            // the row: in registers when short, else read per candidate (L1)
+            constexpr bool kRegRow = D <= 64;
+            const float *xg = p.X + n * D;
+            ulonglong2 xr[kRegRow ? D / 4 : 1];
+            if (kRegRow) {
+                const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(xg);
 #pragma unroll
-        for (int i = 0; i < D / 4; ++i) xr[i] = reinterpret_cast<const ulonglong2 *>(xs)[i];
-        auto fp32 = [&](int col) {
-            const ulonglong2 *c = reinterpret_cast<const ulonglong2 *>(Cs + (size_t)col * p.Dp);
-            unsigned long long a0 = 0ull, a1 = 0ull;
-#pragma unroll
-            for (int i = 0; i < D / 4; ++i) {
-                const ulonglong2 c2 = c[i];
-                unsigned long long d0, d1;
-                asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(xr[i].x), "l"(c2.x));
-                asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(xr[i].y), "l"(c2.y));
-                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
-                asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
+                for (int i = 0; i < (kRegRow ? D / 4 : 1); ++i) xr[i] = __ldg(xp + i);
             }
-            float l0, h0, l1, h1;
-            asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(h0) : "l"(a0));
-            asm("mov.b64 {%0, %1}, %2;" : "=f"(l1), "=f"(h1) : "l"(a1));
-            return (l0 + h0) + (l1 + h1);
-        };
-        // the candidates: the centroids of the masked groups, lanes over the
-        // centroids of one group at a time (ascending index); all K when the
-        // mask holds every group
-        const int G = p.G;
-        auto for_candidates = [&](auto &&fn) {
-            if (q.gmask == ~0ull) {
-                for (int col = lane; col < K; col += 32) fn(col);
-                return;
-            }
-            unsigned long long m = q.gmask;
-            while (m) {
-                const int g = __ffsll((long long)m) - 1;
-                m &= m - 1;
-                if (g >= G) break;
-                for (int col = gs_s[g] + lane; col < gs_s[g + 1]; col += 32) fn(col);
-            }
-        };
-        // each lane: its candidates' two smallest; then the warp's winner and runner-up
-        float s1 = INFINITY, s2 = INFINITY;
-        int i1 = 0x7fffffff;
-        for_candidates([&](int col) {
-            const float sx = fp32(col);
-            if (sx < s1 || (sx == s1 && col < i1)) {
-                s2 = s1;
-                s1 = sx;
-                i1 = col;
-            } else {
-                s2 = fminf(s2, sx);
-            }
-        });
-        float bs = s1;
-        int bi = i1;
-        warp_argmin(bs, bi);
-        const float sec = warp_min(i1 == bi ? s2 : s1);
-        if (sec != INFINITY && unresolved(bs, sec, p)) {
-            double bd = INFINITY;
-            int bj = 0x7fffffff;
+            auto fp32 = [&](int col) {
+                if constexpr (kRegRow)
+                    return settle_fp32<D>(reinterpret_cast<const ulonglong2 (&)[D / 4]>(xr), Cs + (size_t)col * SD);
+                else
+                    return settle_fp32_g<D>(xg, Cs + (size_t)col * SD);
+            };
+            // the candidates: the centroids of the masked groups in ascending
+            // index; all K when the mask holds every group
+            auto for_candidates = [&](auto &&fn) {
+                if (q.gmask == ~0ull) {
+                    for (int col = 0; col < K; ++col) fn(col);
+                    return;
+                }
+                unsigned long long m = q.gmask;
+                while (m) {
+                    const int g = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    if (g >= G) break;
+                    for (int col = gs_s[g]; col < gs_s[g + 1]; ++col) fn(col);
+                }
+            };
+            // smallest (first in ascending order on ties) and runner-up
+            float s1 = INFINITY, s2 = INFINITY;
+            int bi = q.i1;
             for_candidates([&](int col) {
-                if (!unresolved(bs, fp32(col), p)) return;
-                const double d64 = dist2_f64(xs, Cs + (size_t)col * p.Dp, D);
-                if (d64 < bd || (d64 == bd && col < bj)) {
-                    bd = d64;
-                    bj = col;
+                const float sx = fp32(col);
+                if (sx < s1) {
+                    s2 = s1;
+                    s1 = sx;
+                    bi = col;
+                } else {
+                    s2 = fminf(s2, sx);
                 }
             });
-            warp_argmin_d(bd, bj);
-            if (bj != bi) bs = fp32(bj);
-            bi = bj;
-            c_recheck += 1;
-        }
-        if (lane == 0) {
+            float bs = s1;
+            if (s2 != INFINITY && unresolved(s1, s2, p)) {
+                double bd = INFINITY;
+                int bj = bi;
+                for_candidates([&](int col) {
+                    if (!unresolved(s1, fp32(col), p)) return;
+                    const double d64 = settle_fp64(xg, Cs + (size_t)col * SD, D);
+                    if (d64 < bd) {
+                        bd = d64;
+                        bj = col;
+                    }
+                });
+                if (bj != bi) bs = fp32(bj);
+                bi = bj;
+                c_recheck += 1;
+            }
             p.label[n] = bi;
             if (bounds) {
                 p.u[n] = dist_up(bs, p);
@@ -646,18 +834,32 @@ __global__ void __launch_bounds__(kSettleThreads) k_settle(Params p, int first, 
                     p.lbg[n] = q.lb_alt;
                 }
             }
-            if (bi != q.old) {
-                c_changed += 1;
-                if (!first) {
-                    const int slot = atomicAdd(&ctrl->moved_count, 1);
-                    p.moved[slot] = (int32_t)n;
-                    p.moved_old[slot] = q.old;
+            // label changes: one slot reservation per group of converged lanes
+            const bool moved = bi != q.old;
+            c_changed += moved ? 1 : 0;
+            if (!first) {
+                const unsigned am = __activemask();
+                const unsigned mm = __ballot_sync(am, moved);
+                if (mm) {
+                    const int lane = threadIdx.x & 31, leader = __ffs(am) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&ctrl->moved_count, __popc(mm));
+                    base = __shfl_sync(am, base, leader);
+                    if (moved) {
+                        const int slot = base + __popc(mm & ((1u << lane) - 1u));
+                        p.moved[slot] = (int32_t)n;
+                        p.moved_old[slot] = q.old;
+                    }
                 }
             }
         }
-        __syncwarp();  // the row buffer is reused
     }
-    if (lane == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c_changed += __shfl_xor_sync(0xffffffffu, c_changed, o);
+        c_recheck += __shfl_xor_sync(0xffffffffu, c_recheck, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
         if (c_changed) atomicAdd(&ctrl->n_changed, c_changed);
         if (c_recheck) atomicAdd(&ctrl->n_recheck, c_recheck);
     }
@@ -711,8 +913,8 @@ bool plan(const Params &p, size_t smem_limit, TcCfg &cfg, size_t &smem) {
     const size_t NA = p.D / 64;
     const size_t b_bytes = 2 * NA * (size_t)cfg.Kp * 128;
     const size_t a_stage = 2 * NA * (size_t)kAtomBytes;
-    const size_t cn_bytes = (size_t)cfg.Kp * 4;
-    const size_t gs_bytes = (((size_t)p.G + 1) * 4 + 15) & ~size_t(15);
+    const size_t cn_bytes = (size_t)cfg.Kp * 8;  // norms and group-opening penalties
+    const size_t gs_bytes = (((size_t)cfg.Kp / 32) * 4 + 15) & ~size_t(15);  // group-start masks
     const size_t stage_bytes = (size_t)kGroups * kTM * (p.Gp + 1) * 4;
     const size_t fixed = 1024 + b_bytes + cn_bytes + gs_bytes + stage_bytes + 64 * 8 + 64;
     if (fixed + 2 * a_stage > smem_limit) return false;
@@ -772,10 +974,17 @@ cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_don
 }  // namespace
 
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms) {
-    const size_t smem = (size_t)p.K * p.Dp * 4 + (size_t)(kSettleThreads / 32) * p.D * 4 + (size_t)(p.G + 1) * 4;
-    auto kern = p.D == 64 ? k_settle<64> : k_settle<128>;
     if (p.D != 64 && p.D != 128) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // compact the request bitmap (one warp per 32 words), then one thread per request
+    const int64_t words = (p.N + 31) / 32;
+    const int64_t gblocks = std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, (int64_t)num_sms * 8));
+    count_launch();
+    k_settle_gather<<<(unsigned)gblocks, 256, 0, s>>>(p, respect_done);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)p.K * (p.D + 4) * 4 + (size_t)(p.G + 1) * 4;
+    auto kern = p.D == 64 ? k_settle<64> : k_settle<128>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSettleThreads, smem);

@@ -239,6 +239,18 @@ cudaError_t launch_bounds_out(const Params &p, cudaStream_t s, float *u, float *
     k_bounds_out<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p, u, lbg, lb);
     return cudaGetLastError();
 }
+// bfloat16 bit patterns -> FP32 (exact: a bfloat16 is the top half of an FP32)
+__global__ void k_bf16_to_f32(const uint16_t *in, int64_t n, float *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __uint_as_float((uint32_t)in[i] << 16);
+}
+
+cudaError_t launch_bf16_to_f32(const uint16_t *in, int64_t n, float *out, cudaStream_t s, int num_sms) {
+    count_launch();
+    k_bf16_to_f32<<<num_sms * 8, 256, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t s, int num_sms) {
     int64_t grid = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8);
     count_launch();

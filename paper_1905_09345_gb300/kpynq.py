@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libkpynq.so")
 
 KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ESTATE = 0, -1, -2, -3, -4, -5
 KM_ALGO_FILTERED, KM_ALGO_LLOYD = 0, 1
+KM_DTYPE_F32, KM_DTYPE_BF16 = 0, 1
 KM_GROUP_CONTIGUOUS = 0
 KM_DENSE_AUTO, KM_DENSE_FP32 = 0, 1
 KM_PATH_FILTERED, KM_PATH_DENSE_FP32, KM_PATH_DENSE_TC = 0, 1, 2
@@ -36,7 +37,8 @@ class KMeansError(RuntimeError):
 class kmeans_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("grouping", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("dense", ctypes.c_int32),
-                ("dense_switch", ctypes.c_float), ("reserved", ctypes.c_int64 * 5)]
+                ("dense_switch", ctypes.c_float), ("dtype", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 class kmeans_problem(ctypes.Structure):
@@ -68,6 +70,8 @@ def lib():
         vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         L.kmeans_default_options.argtypes = [ctypes.POINTER(kmeans_options)]
         L.kmeans_default_options.restype = None
+        L.kmeans_selftest_sqrt.argtypes = [ctypes.POINTER(i64)]
+        L.kmeans_selftest_sqrt.restype = ctypes.c_int
         L.kmeans_init.argtypes = [ctypes.POINTER(vp), vp, i64, i32, i32, i32, vp, ctypes.POINTER(kmeans_options)]
         L.kmeans_init.restype = ctypes.c_int
         L.kmeans_iterate.argtypes = [vp, ctypes.POINTER(kmeans_iter_stats)]
@@ -147,6 +151,24 @@ def kmeans_default_options() -> kmeans_options:
     o = kmeans_options()
     lib().kmeans_default_options(ctypes.byref(o))
     return o
+
+
+def _dtype_of(X, dtype):
+    """KM_DTYPE_* of X: explicit, else bfloat16 for a torch bfloat16 tensor,
+    else FP32 (a uint16 numpy array of bfloat16 bit patterns needs
+    dtype=KM_DTYPE_BF16)."""
+    if dtype is not None:
+        return int(dtype)
+    return KM_DTYPE_BF16 if str(getattr(X, "dtype", "")) == "torch.bfloat16" else KM_DTYPE_F32
+
+
+
+def kmeans_selftest_sqrt() -> int:
+    """Failures of the square-root bounds over every non-negative float on the
+    current device (0 expected)."""
+    v = ctypes.c_int64(-1)
+    _check(lib().kmeans_selftest_sqrt(ctypes.byref(v)), None)
+    return v.value
 
 
 def kmeans_init(X, N: int, D: int, K: int, G: int, init_centroids, opt: kmeans_options | None = None):
@@ -261,7 +283,8 @@ class KMeans:
     this object)."""
 
     def __init__(self, X, C0, G: int, *, algo: int = KM_ALGO_FILTERED, stream=None, validate: bool = False,
-                 profile: bool = False, dense: int = KM_DENSE_AUTO, dense_switch: float = 0.0):
+                 profile: bool = False, dense: int = KM_DENSE_AUTO, dense_switch: float = 0.0,
+                 dtype: int | None = None):
         N, D = X.shape
         K = C0.shape[0]
         opt = kmeans_default_options()
@@ -270,6 +293,7 @@ class KMeans:
         opt.profile = int(profile)
         opt.dense = dense
         opt.dense_switch = dense_switch
+        opt.dtype = _dtype_of(X, dtype)
         if stream is not None:
             opt.stream = stream if isinstance(stream, int) else stream.cuda_stream
         self._keep = (X, C0)
@@ -387,7 +411,7 @@ class KMeansBatch:
     the autotuner's cache file (None: the library's default switch)."""
 
     def __init__(self, problems, algo: int = KM_ALGO_FILTERED, stream=None, dense: int = KM_DENSE_AUTO,
-                 dense_switch: float = 0.0, tune_cache: str | None = None):
+                 dense_switch: float = 0.0, tune_cache: str | None = None, dtype: int | None = None):
         arr = (kmeans_problem * len(problems))()
         self._keep = []
         for i, (X, C0, G) in enumerate(problems):
@@ -400,6 +424,7 @@ class KMeansBatch:
         opt.algo = algo
         opt.dense = dense
         opt.dense_switch = dense_switch
+        opt.dtype = _dtype_of(problems[0][0], dtype) if problems else KM_DTYPE_F32
         if stream is not None:
             opt.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self.b = kmeans_batch_init(arr, opt, tune_cache)

@@ -101,6 +101,11 @@ def to_bf16(a: np.ndarray) -> np.ndarray:
     return np.where(np.isnan(a), a, out)
 
 
+def bf16_bits(a: np.ndarray) -> np.ndarray:
+    """The uint16 bfloat16 bit patterns of ``to_bf16(a)`` (storage format)."""
+    return (to_bf16(a).view(np.uint32) >> 16).astype(np.uint16)
+
+
 # ---------------------------------------------------------------------------
 # the five measured workloads (sizes can be reduced for tests)
 # ---------------------------------------------------------------------------

@@ -90,6 +90,23 @@ def test_init_rejects_null_and_bad_options(L):
     with pytest.raises(L.KMeansError) as e:
         L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
     assert e.value.status == L.KM_EINVAL
+    for field, bad in (("dtype", 7), ("dtype", -1), ("pad0", 1)):
+        opt = L.kmeans_default_options()
+        setattr(opt, field, bad)
+        with pytest.raises(L.KMeansError) as e:
+            L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
+        assert e.value.status == L.KM_EINVAL, field
+    assert L.kmeans_default_options().dtype == L.KM_DTYPE_F32
+
+
+def test_dtype_inference():
+    from paper_1905_09345_gb300 import kpynq
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    assert kpynq._dtype_of(np.zeros((2, 2), np.float32), None) == kpynq.KM_DTYPE_F32
+    assert kpynq._dtype_of(np.zeros((2, 2), np.uint16), kpynq.KM_DTYPE_BF16) == kpynq.KM_DTYPE_BF16
+    assert kpynq._dtype_of(torch.zeros(2, 2, dtype=torch.bfloat16), None) == kpynq.KM_DTYPE_BF16
+    assert kpynq._dtype_of(torch.zeros(2, 2), None) == kpynq.KM_DTYPE_F32
 
 
 def test_null_context_calls(L):
