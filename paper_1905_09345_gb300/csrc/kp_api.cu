@@ -525,6 +525,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         INIT_CUDA(dalloc(c, &p.lbg, (size_t)N));
         INIT_CUDA(dalloc(c, &p.stamp, (size_t)N));
         INIT_CUDA(dalloc(c, &p.lb, (size_t)N * p.Gp));
+        INIT_CUDA(cudaMemsetAsync(p.lb, 0, (size_t)N * p.Gp * 4, c->stream));  // padding columns stay 0
         INIT_CUDA(dalloc(c, &p.queue, (size_t)N));
         // survivor queue buckets: labels >> bshift, at most 4096 buckets
         p.bshift = 0;
@@ -583,7 +584,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.eps_lo = f32_dn(1.0 - eps);
     p.tiny = std::ldexp((float)(D + 4), -149);
     c->use_tc = o.dense == KM_DENSE_AUTO && (reinterpret_cast<uintptr_t>(p.X) & 15) == 0 &&
-                dense_tc_eligible(p, c->smem_optin);
+                (dense_tc_eligible(p, c->smem_optin) || dense_tcb_eligible(p, c->smem_optin));
     // default switch: the tensor-core dense pass costs about as much as the
     // survivor kernel with 70% of the points surviving; the FP32 one more
     p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.7f : 0.9f);
@@ -604,6 +605,12 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         INIT_CUDA(dalloc(c, &sqq, (size_t)N));
         p.sbits = sb;
         p.squeue = sqq;
+        if (K > 256) {  // the centroid blocks stream from a split copy made each pass
+            const int kp = dense_tcb_kp(p);
+            INIT_CUDA(dalloc(c, &p.Ch, (size_t)kp * D));
+            INIT_CUDA(dalloc(c, &p.Cl, (size_t)kp * D));
+            INIT_CUDA(dalloc(c, &p.cnorm, (size_t)K));
+        }
     }
 
     if (o.validate) {

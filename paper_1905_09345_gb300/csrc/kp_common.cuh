@@ -73,7 +73,9 @@ struct SettleReq {
     int32_t old;     // label before this pass (-1: none)
     int32_t i1;      // tensor-core winner (the bounds were written for it)
     float lb_alt;    // group bound that holds for every column (from the smallest estimate)
-    unsigned long long gmask;  // groups that can hold the winner (all ones: every group)
+    unsigned long long gmask;  // groups that can hold the winner (all ones: every group;
+                               // zero: the groups g with lb[n][g] <= lim)
+    float lim;       // bound of the window's edge (used when gmask is zero)
 };
 
 // Everything a kernel needs, passed by value.
@@ -111,6 +113,8 @@ struct Params {
     int32_t nbucket, bshift;
     struct SettleReq *sreq;  // N, indexed by row: rows the tensor-core pass left to the exact settle
     uint32_t *sbits;     // ceil(N / 128) * 4 words: bit n set = row n has a settle request
+    uint16_t *Ch, *Cl;   // Kp x D bfloat16 halves of C (tensor-core pass with K > 256)
+    float *cnorm;        // K: ||c||^2 of that pass
     int32_t *squeue;     // N: the rows with a request, compacted from the bitmap
     int32_t *perm;       // N: point ids sorted by label (full recompute of the cluster sums)
     int32_t *slab;       // N: their labels
@@ -329,6 +333,10 @@ int dense_dp(int D);  // register tile width used for D (0 = generic path)
 cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                                 int if_dense = 0);
 bool dense_tc_eligible(const Params &p, size_t smem_limit);
+bool dense_tcb_eligible(const Params &p, size_t smem_limit);
+int dense_tcb_kp(const Params &p);  // padded K of the split centroid copy
+cudaError_t launch_dense_tcb(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
+                             size_t smem_limit, int if_dense);
 cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
                            int num_sms);
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,

@@ -33,24 +33,15 @@
 //   ||c||^2 is an FP32 sum of squares and the final fma rounds once:
 //     |t~ - t| <= (6.1 2^-16 + (6D+1) 2^-23) ||x|| ||c|| + (D+3) 2^-24 ||c||^2,
 //   used with a 1.25x margin as E(x).
-#include <cuda.h>
-#include <cuda_bf16.h>
-#include <cudaTypedefs.h>
-
-#include <mutex>
-
-#include "kp_common.cuh"
+#include "kp_tc.cuh"
 
 namespace kp {
 
 namespace {
 
-constexpr int kTM = 128;          // points per tile
 constexpr int kEpiWarps = 4;      // warps per epilogue group
 constexpr int kGroups = 2;        // epilogue groups = TMEM buffers
 constexpr int kTcThreads = 64 + kGroups * kEpiWarps * 32;
-constexpr uint32_t kPolls = 1u << 22;
-constexpr int kAtomBytes = kTM * 128;  // one 64-element bfloat16 column block of a tile
 
 struct TcCfg {
     int Kp;        // centroid rows in shared memory (multiple of 32, <= 256)
@@ -63,184 +54,6 @@ struct TcCfg {
     float e_c2;    // 1.25 (D+3) 2^-24, rounded up
     float xn_lo, xn_hi;  // relative error of ||x||^2 from the split copy
 };
-
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
-    return d;
-}
-__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-// bounded wait; on time-out records KM_ETIMEOUT and returns false
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, Ctrl *ctrl) {
-    for (uint32_t i = 0; i < kPolls; ++i)
-        if (mbar_try_wait(b, parity)) return true;
-    atomicExch(&ctrl->err, (int)KM_ETIMEOUT);
-    return false;
-}
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *m, int c0, int c1, uint64_t *b) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)m), "r"(c0), "r"(c1), "r"(smem_u32(b))
-        : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Asynchronous TMEM read of 32 columns; the registers may be used only after
-// tmem_wait32 on the same array (which names them, so that the compiler
-// cannot move their uses above the wait).
-__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
-}
-
-// byte offset of the 16-byte chunk holding bfloat16 elements [8q, 8q+8) of
-// `row` in a 128-byte-swizzled K-major tile (64 elements per 128-byte row)
-__device__ __forceinline__ uint32_t swz_chunk(int row, int q, int atom_bytes) {
-    return (uint32_t)((q >> 3) * atom_bytes + row * 128 + (((q & 7) ^ (row & 7)) << 4));
-}
-
-__device__ __forceinline__ void split8(const float *v, uint4 &h, uint4 &l) {
-    uint32_t hw[4], lw[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]), h1 = __float2bfloat16_rn(v[2 * i + 1]);
-        __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
-        __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
-        hw[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        lw[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    }
-    h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-}
-__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-
-// ||x||^2 of one row of the split A tile, from x_h + x_l
-template <int D>
-__device__ __forceinline__ float row_norm2(const uint8_t *Ah, const uint8_t *Al, int row) {
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < D / 8; ++q) {
-        const uint4 h = *reinterpret_cast<const uint4 *>(Ah + swz_chunk(row, q, kAtomBytes));
-        const uint4 l = *reinterpret_cast<const uint4 *>(Al + swz_chunk(row, q, kAtomBytes));
-        const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float v0 = bf_lo(hw[i]) + bf_lo(lw[i]);
-            const float v1 = bf_hi(hw[i]) + bf_hi(lw[i]);
-            a0 = fmaf(v0, v0, a0);
-            a1 = fmaf(v1, v1, a1);
-        }
-    }
-    return a0 + a1;
-}
-
-// Running scan of one row over a run of accumulator columns: the per-group
-// minima (stored into the row's shared-memory slots as each group closes),
-// and the smallest value with its index and the runner-up, in two independent
-// chains (even and odd columns).  Branch-free: pen[c] is +inf where column c
-// opens a group (0 elsewhere), so that gm + pen restarts the running minimum,
-// and the closing minimum is stored by a predicated shared store.  A row is
-// scanned as two such runs (the two halves of its columns) interleaved column
-// by column, for instruction-level parallelism; merge() joins them.
-struct RowScan {
-    float b1[2], b2[2];
-    int i1[2];
-    float gm;     // minimum of the open group
-    uint32_t rp;  // shared-memory address of the open group's slot
-
-    __device__ __forceinline__ void init(const float *slot) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            b1[c] = INFINITY;
-            b2[c] = INFINITY;
-            i1[c] = 0;  // kept when no column is below +inf (then column 0)
-        }
-        gm = INFINITY;
-        rp = smem_u32(slot);
-    }
-    __device__ __forceinline__ void col(float acc, float cnv, float pen, int c, int jpar) {
-        const float t = fmaf(-2.f, acc, cnv);
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.f32 p, %2, 0f00000000;\n\t@p st.shared.f32 [%0], %1;\n\t"
-            "@p add.u32 %0, %0, 4;\n\t}"
-            : "+r"(rp)
-            : "f"(gm), "f"(pen)
-            : "memory");
-        gm = fminf(__fadd_rn(gm, pen), t);
-        b2[jpar] = fminf(b2[jpar], fmaxf(b1[jpar], t));
-        const bool lt = t < b1[jpar];
-        b1[jpar] = lt ? t : b1[jpar];
-        i1[jpar] = lt ? c : i1[jpar];
-    }
-    // store the open group's minimum
-    __device__ __forceinline__ void close() const {
-        asm volatile("st.shared.f32 [%0], %1;" ::"r"(rp), "f"(gm) : "memory");
-    }
-    // winner (lowest index among equal values) and runner-up of both chains
-    __device__ __forceinline__ void result(float &w1, int &wi, float &w2) const {
-        const bool odd = b1[1] < b1[0] || (b1[1] == b1[0] && i1[1] < i1[0]);
-        w1 = odd ? b1[1] : b1[0];
-        wi = odd ? i1[1] : i1[0];
-        w2 = fminf(fminf(b2[0], b2[1]), fmaxf(b1[0], b1[1]));
-    }
-};
-
-// two runs of 32 columns each (chunks ca of run A and cb of run B), column by
-// column; cn / pen read four columns at a time
-__device__ __forceinline__ void scan_pair(RowScan &A, const uint32_t (&ra)[32], int ca, RowScan &B,
-                                          const uint32_t (&rb)[32], int cb, const float *cn, const float *pen) {
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-        const float4 na = *reinterpret_cast<const float4 *>(cn + ca + j);
-        const float4 pa = *reinterpret_cast<const float4 *>(pen + ca + j);
-        const float4 nb = *reinterpret_cast<const float4 *>(cn + cb + j);
-        const float4 pb = *reinterpret_cast<const float4 *>(pen + cb + j);
-        const float nav[4] = {na.x, na.y, na.z, na.w}, pav[4] = {pa.x, pa.y, pa.z, pa.w};
-        const float nbv[4] = {nb.x, nb.y, nb.z, nb.w}, pbv[4] = {pb.x, pb.y, pb.z, pb.w};
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            A.col(__uint_as_float(ra[j + jj]), nav[jj], pav[jj], ca + j + jj, jj & 1);
-            B.col(__uint_as_float(rb[j + jj]), nbv[jj], pbv[jj], cb + j + jj, jj & 1);
-        }
-    }
-}
-__device__ __forceinline__ void scan_one(RowScan &A, const uint32_t (&ra)[32], int ca, const float *cn,
-                                         const float *pen) {
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-        const float4 na = *reinterpret_cast<const float4 *>(cn + ca + j);
-        const float4 pa = *reinterpret_cast<const float4 *>(pen + ca + j);
-        const float nav[4] = {na.x, na.y, na.z, na.w}, pav[4] = {pa.x, pa.y, pa.z, pa.w};
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) A.col(__uint_as_float(ra[j + jj]), nav[jj], pav[jj], ca + j + jj, jj & 1);
-    }
-}
-
-// group of column `col` from the boundary masks (contiguous groups)
-__device__ __forceinline__ int group_of(const uint32_t *bm, int col) {
-    const int c = col >> 5;
-    int g = __popc(bm[c] & ((2u << (col & 31)) - 1u));
-    for (int i = 0; i < c; ++i) g += __popc(bm[i]);
-    return g;
-}
 
 template <int D>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -525,6 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         // i1's group (which now keeps i1) and the winner's group
                         rq.lb_alt = sqrt_lo(__fsub_rd(__fadd_rd(xlo, b1), E));
                         rq.gmask = gmask;
+                        rq.lim = 0.f;
                         p.sreq[n] = rq;
                     }
                 }
@@ -724,7 +538,7 @@ __global__ void k_settle_gather(Params p, int respect_done) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kSettleThreads, 2) k_settle(Params p, int first, int respect_done) {
+__global__ void __launch_bounds__(kSettleThreads, 2) k_settle(Params p, int first, int respect_done, int staged) {
     extern __shared__ __align__(16) float sm_settle[];  // C (K rows, stride SD) | group starts
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
@@ -740,16 +554,18 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle(Params p, int firs
     const int64_t nthreads = (int64_t)gridDim.x * kSettleThreads;
     if ((int64_t)blockIdx.x * kSettleThreads >= total) return;  // uniform per block
     const int K = p.K, G = p.G;
-    // C with a row stride of D + 4 floats: 16-byte reads of different rows by
-    // the threads of a warp spread over the banks
-    constexpr int SD = D + 4;
-    float *Cs = sm_settle;
-    int32_t *gs_s = reinterpret_cast<int32_t *>(sm_settle + (size_t)K * SD);
-    for (int i = threadIdx.x; i < K * (D / 4); i += kSettleThreads) {
-        const int row = i / (D / 4), q4 = i - row * (D / 4);
-        reinterpret_cast<float4 *>(Cs + (size_t)row * SD)[q4] =
-            __ldg(reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp) + q4);
-    }
+    // C staged with a row stride of D + 4 floats (16-byte reads of different
+    // rows by the threads of a warp spread over the banks), or read from
+    // global memory when it does not fit
+    const int SD = staged ? D + 4 : p.Dp;
+    const float *Cs = staged ? sm_settle : p.C;
+    int32_t *gs_s = reinterpret_cast<int32_t *>(sm_settle + (staged ? (size_t)K * SD : 0));
+    if (staged)
+        for (int i = threadIdx.x; i < K * (D / 4); i += kSettleThreads) {
+            const int row = i / (D / 4), q4 = i - row * (D / 4);
+            reinterpret_cast<float4 *>(sm_settle + (size_t)row * SD)[q4] =
+                __ldg(reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp) + q4);
+        }
     for (int i = threadIdx.x; i <= G; i += kSettleThreads) gs_s[i] = p.gstart[i];
     __syncthreads();
     const bool bounds = p.algo == KM_ALGO_FILTERED;
@@ -784,8 +600,15 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle(Params p, int firs
             // the candidates: the centroids of the masked groups in ascending
             // index; all K when the mask holds every group
             auto for_candidates = [&](auto &&fn) {
-                if (q.gmask == ~0ull) {
+                if (q.gmask == ~0ull || (q.gmask == 0ull && !bounds)) {
                     for (int col = 0; col < K; ++col) fn(col);
+                    return;
+                }
+                if (q.gmask == 0ull) {  // the groups whose bound is within the window's edge
+                    const float *lbr = p.lb + n * p.Gp;
+                    for (int g = 0; g < G; ++g)
+                        if (lbr[g] <= q.lim)
+                            for (int col = gs_s[g]; col < gs_s[g + 1]; ++col) fn(col);
                     return;
                 }
                 unsigned long long m = q.gmask;
@@ -884,20 +707,6 @@ __global__ void k_split_x(const float *X, int64_t n4, uint2 *Xh, uint2 *Xl) {
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void *f = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    });
-    return fn;
-}
-
 int pow2_at_least(int x) {
     int p2 = 32;
     while (p2 < x) p2 <<= 1;
@@ -982,7 +791,10 @@ cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respec
     k_settle_gather<<<(unsigned)gblocks, 256, 0, s>>>(p, respect_done);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)p.K * (p.D + 4) * 4 + (size_t)(p.G + 1) * 4;
+    // C in shared memory when it fits (up to 160 KB), else read from L2
+    const size_t cbytes = (size_t)p.K * (p.D + 4) * 4;
+    const int staged = cbytes <= ((size_t)160 << 10);
+    const size_t smem = (staged ? cbytes : 0) + (size_t)(p.G + 1) * 4;
     auto kern = p.D == 64 ? k_settle<64> : k_settle<128>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -990,7 +802,7 @@ cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respec
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSettleThreads, smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    kern<<<(unsigned)(num_sms * std::max(per_sm, 1)), kSettleThreads, smem, s>>>(p, first, respect_done);
+    kern<<<(unsigned)(num_sms * std::max(per_sm, 1)), kSettleThreads, smem, s>>>(p, first, respect_done, staged);
     return cudaGetLastError();
 }
 
@@ -1012,6 +824,7 @@ cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint1
 
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense) {
+    if (p.K > 256) return launch_dense_tcb(p, s, first, respect_done, num_sms, smem_limit, if_dense);
     switch (p.D) {
     case 64: return launch_t<64>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
     case 128: return launch_t<128>(p, s, first, respect_done, num_sms, smem_limit, if_dense);

@@ -48,9 +48,33 @@ def get_labels(km):
     return km.labels(out).cpu().numpy()
 
 
-def tc_expected(D, K, G, smem=232448):
-    """Mirror of the tensor-core kernel's eligibility (shape and shared memory)."""
-    if D % 64 or D > 128 or K > 256:
+def tc_expected(D, K, G, smem=232448, algo=0):
+    """Mirror of the tensor-core kernels' eligibility (shape and shared memory):
+    one accumulator block for K <= 256, streamed centroid blocks above (the
+    filtered method only)."""
+    if D % 64 or D > 128:
+        return False
+    if K > 256:
+        if algo != 0:
+            return False
+        Kp = (K + 127) // 128 * 128
+        if Kp > 4096:
+            return False
+        most = 0
+        for j in range(Kp // 64):
+            c0, c1 = 64 * j, min(64 * (j + 1), K) - 1
+            if c0 >= K:
+                break
+            most = max(most, c1 * G // K - c0 * G // K + 1)
+        srow = (most + 2) | 1
+        na = D // 64
+        a_stage = b_stage = 2 * na * 128 * 128
+        stage = 2 * 4 * 32 * srow * 4
+        for bst in (2, 1):
+            off = 2 * a_stage + bst * b_stage + Kp * 8 + (Kp // 32 * 4 + 15) // 16 * 16 + stage
+            off = (off + 7) // 8 * 8 + (4 + 2 * bst + 8 + 1) * 8 + 16
+            if 1024 + off <= smem:
+                return True
         return False
     Kp = (K + 31) // 32 * 32
     na = D // 64
@@ -105,7 +129,7 @@ def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None, dense
         if t > 0 and algo == 0 and dense_switch >= 1.0:
             assert st["path"] == kp.KM_PATH_FILTERED, (t, st["path"])
         if t == 0 or algo == kp.KM_ALGO_LLOYD:
-            want = kp.KM_PATH_DENSE_TC if (dense == 0 and tc_expected(D, K, G)) else kp.KM_PATH_DENSE_FP32
+            want = kp.KM_PATH_DENSE_TC if (dense == 0 and tc_expected(D, K, G, algo=algo)) else kp.KM_PATH_DENSE_FP32
             assert st["path"] == want, (t, st["path"], want)
         stats.append(st)
         prev = ref
@@ -416,3 +440,50 @@ def test_final_assignment_stats(kp):
     with pytest.raises(kp.KMeansError):
         km.final_stats()
     km.close()
+
+
+# more centroids than one accumulator block: the tensor-core pass streams the
+# centroids in blocks of 128 (ragged tails, several tiles per CTA, G over 64,
+# a single group)
+KBLOCKED = [
+    (40000, 64, 300, 30, 4),
+    (100003, 128, 520, 100, 3),
+    (20000, 64, 1024, 103, 3),
+    (5000, 128, 257, 1, 3),
+]
+
+
+@pytest.mark.parametrize("N,D,K,G,iters", KBLOCKED, ids=[f"N{e[0]}_D{e[1]}_K{e[2]}_G{e[3]}" for e in KBLOCKED])
+def test_kblocked_tensor_core_lockstep(kp, N, D, K, G, iters):
+    rng = np.random.default_rng(N + K)
+    X, _ = synth.gaussian_mixture(rng, N, D, K, centre_range=20.0, scale="blob_lognormal", scale_args=(0.0, 0.5))
+    C0 = synth.sample_init(rng, X, K)
+    st = lockstep(kp, X, C0, G, iters, check_bounds=(N * K <= 25_000_000))
+    assert st[0]["path"] == kp.KM_PATH_DENSE_TC
+
+
+def test_kblocked_matches_fp32_engine_and_near_ties(kp):
+    """Points half-way between two of 300 centroids: the streamed tensor-core
+    pass must queue them, and the settle (candidates from the written group
+    bounds) must give the oracle's labels; the whole fit equals the FP32
+    engine's."""
+    rng = np.random.default_rng(77)
+    K, N, D = 300, 30000, 64
+    C0 = (rng.uniform(-3, 3, (K, D)) + 40.0).astype(np.float32)
+    a = rng.integers(0, K, N)
+    b = (a + 1 + rng.integers(0, K - 1, N)) % K
+    w = (0.5 + rng.uniform(-1e-6, 1e-6, N))[:, None]
+    X = (w * C0[a] + (1 - w) * C0[b] + rng.normal(0, 1e-4, (N, D))).astype(np.float32)
+    X[: N // 8] = (0.5 * C0[a[: N // 8]] + 0.5 * C0[b[: N // 8]]).astype(np.float32)
+    st = lockstep(kp, X, C0, 30, 2)
+    assert st[0]["n_recheck"] > 0 and st[0]["n_settle"] > 0
+    outs = []
+    for dense in (0, 1):
+        km = kp.KMeans(dev(X), dev(C0), 30, dense=dense)
+        lab = torch.empty(N, dtype=torch.int32, device="cuda")
+        r = km.fit(6, 0.0, lab)
+        outs.append((r.n_iter, lab.cpu().numpy(), r.objective))
+        km.close()
+    assert outs[0][0] == outs[1][0]
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert abs(outs[0][2] - outs[1][2]) <= 1e-9 * outs[1][2]
