@@ -51,10 +51,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "highdim4m", "batched"],
+    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "highdim4m", "batched", "gsweep"],
                     help="aniso1m: the 1M-point anisotropic job (default line); highdim4m: 4M points, "
                          "D=128, K=1024, stored as bfloat16; batched: 512 independent problems of uneven "
-                         "N, D, K fitted by one graph launch")
+                         "N, D, K fitted by one graph launch; gsweep: the 1M job at G in {1, K/20, K/10, "
+                         "K/5, K} (throughput and skip fraction per G)")
     ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the profiled pass (every kernel launched eagerly, timed with CUDA "
@@ -132,7 +133,7 @@ class ClockSampler:
     def summary(self) -> dict:
         if not self.proc or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
+        sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -143,13 +144,26 @@ class ClockSampler:
                 smax.append(float(f[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(f[3]))
+            except ValueError:
+                pass
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "reasons": sorted(reasons), "power_w_mean": statistics.mean(pw) if pw else None}
+
+
+def energy_of(value: float, clocks: dict) -> dict | None:
+    """points*iters per joule from the mean board power sampled during the timed steps."""
+    w = clocks.get("power_w_mean")
+    if not w:
+        return None
+    return {"value": value / w, "unit": "points*iters/J", "mean_power_w": w, "samples": clocks.get("samples"),
+            "source": "nvidia-smi power.draw every 200 ms during the timed steps (whole board)"}
 
 
 def gpu_uuid():
@@ -240,12 +254,14 @@ def source_sha(files) -> str:
 
 
 KERNEL_SOURCES = {
-    "dense_assign": ["paper_1905_09345_gb300/csrc/kp_dense_tc.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "dense_assign": ["paper_1905_09345_gb300/csrc/kp_dense_tc.cu", "paper_1905_09345_gb300/csrc/kp_tc.cuh",
+                     "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "apply_moves": ["paper_1905_09345_gb300/csrc/kp_dense.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "filter": ["paper_1905_09345_gb300/csrc/kp_filter.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "survivor": ["paper_1905_09345_gb300/csrc/kp_survivor_tp.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "update": ["paper_1905_09345_gb300/csrc/kp_update.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
-    "settle": ["paper_1905_09345_gb300/csrc/kp_dense_tc.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "settle": ["paper_1905_09345_gb300/csrc/kp_dense_tc.cu", "paper_1905_09345_gb300/csrc/kp_tc.cuh",
+               "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "stats": ["paper_1905_09345_gb300/csrc/kp_stats.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
 }
 
@@ -519,6 +535,7 @@ def run_ours(args):
                    "l2": f"flushed between steps (256 MiB write); X is {w.N * w.D * 4 >> 20} MiB > L2",
                    "parallelism": f"replicas x{ws}"},
         "clocks": clk.summary(),
+        "energy": energy_of(value, clk.summary()),
         "e2e": e2e,
         "gpu_launches": kern,
         "roofline": roof,
@@ -618,11 +635,63 @@ def run_batched(args):
                    "step": "kmeans_batch_reset + kmeans_batch_fit (one graph launch)",
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws_}"},
         "clocks": clk.summary(),
+        "energy": energy_of(value, clk.summary()),
         "init_s": init_s, "tuned_switches": switches,
         "sequential_single_contexts": {"value": seq_value, "s_per_step": statistics.mean(seq)},
         "vs_sequential": value / seq_value,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_gsweep(args):
+    """The anisotropic job with the number of centroid groups swept (the
+    method's group-filter granularity): throughput and the fraction of
+    distance evaluations the filters skip, per G; the dense switch never
+    fires after iteration 0 here, so that the filters alone do the work."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1905_09345_gb300 import kpynq
+    w = make_workload(args, rank)
+    dev = torch.device("cuda", local)
+    X = device_points(w, dev)
+    C0 = torch.from_numpy(w.C0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    lab = torch.empty(w.N, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    K = w.K
+    rows = []
+    with ClockSampler(gpu_uuid()) as clk:
+        for G in sorted({1, max(1, K // 20), max(1, K // 10), max(1, K // 5), K}):
+            for switch, label in ((0.0, "default switch"), (1.0, "filters only")):
+                km = kpynq.KMeans(X, C0, G, stream=stream, dense_switch=switch)
+                times, iters, nd = [], [], 0
+                for i in range(args.warmup + args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    km.reset(C0)
+                    r = km.fit(w.max_iter, w.tol, lab, with_stats=False)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if i >= args.warmup:
+                        times.append(e0.elapsed_time(e1))
+                        iters.append(r.n_iter)
+                st = km.stats(0, iters[-1])
+                km.close()
+                nd = sum(s_["n_dist"] for s_ in st)
+                ms = statistics.mean(times)
+                rows.append({"G": G, "switch": label, "ms_per_fit": ms, "iters": iters[-1],
+                             "points_iters_per_s": w.N * statistics.mean(iters) / (ms / 1e3),
+                             "skip_fraction": 1.0 - nd / (w.N * K * len(st))})
+    if rank == 0:
+        best = max(rows, key=lambda r_: r_["points_iters_per_s"])
+        print(json.dumps({"metric": METRIC, "value": best["points_iters_per_s"], "unit": UNIT, "n_gpus": ws,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_fit"],
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": w.name + "_gsweep", "N": w.N, "D": w.D,
+                                                          "K": K, "best_G": best["G"], "best": best["switch"]},
+                          "clocks": clk.summary(), "sweep": rows}), flush=True)
 
 
 def main():
@@ -631,6 +700,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "gsweep":
+        run_gsweep(args)
     else:
         run_ours(args)
 

@@ -54,3 +54,10 @@ def test_aggregate_max_time_sum_units_two_ranks():
 def test_aggregate_single_rank_is_identity():
     import bench
     assert bench.aggregate(7.5, 42.0, 1) == (7.5, 42.0)
+
+
+def test_energy_per_point_iteration():
+    import bench
+    e = bench.energy_of(3.0e9, {"power_w_mean": 600.0, "samples": 7})
+    assert e["value"] == 3.0e9 / 600.0 and e["unit"] == "points*iters/J"
+    assert bench.energy_of(1.0, {"power_w_mean": None}) is None
