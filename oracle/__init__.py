@@ -15,6 +15,10 @@ Two independent C implementations, each written from its definition:
   filter, point-level filter, distance calculator, bound refresh; Sec. I), in
   FP64, with per-iteration skip counters.
 
+* ``mlp.py`` (O3): the learned group proposal's MLP (GELU layers, softmax
+  cross-entropy, Adam) in numpy FP64 -- a layered form of this build, not in
+  the paper; the filtered method's labels do not depend on it.
+
 Pins (``tests/test_oracle_*.py``, ``-m "not gpu"``): closed forms (K = 1 mean,
 K = N zero objective), a hand-derived worked example (``tests/golden``),
 scipy ``cdist`` and scikit-learn's Lloyd as independent library routines,
