@@ -51,16 +51,18 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "highdim4m", "batched", "gsweep"],
+    ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "highdim4m", "batched", "gsweep", "proposal"],
                     help="aniso1m: the 1M-point anisotropic job (default line); highdim4m: 4M points, "
                          "D=128, K=1024, stored as bfloat16; batched: 512 independent problems of uneven "
                          "N, D, K fitted by one graph launch; gsweep: the 1M job at G in {1, K/20, K/10, "
-                         "K/5, K} (throughput and skip fraction per G)")
+                         "K/5, K} (throughput and skip fraction per G); proposal: the 8.4M-point family "
+                         "(D=32, K=4096, G=410), fits with and without the learned group proposal")
     ap.add_argument("--problems", type=int, default=512, help="batched workload: number of problems")
     ap.add_argument("--profile-only", action="store_true",
                     help="run only the profiled pass (every kernel launched eagerly, timed with CUDA "
                          "events) and print its breakdown: the command the ncu launch list is taken on")
     ap.add_argument("--n", type=int, default=None, help="points (default: the full workload)")
+    ap.add_argument("--train-epochs", type=int, default=3, help="proposal workload: MLP training epochs (host)")
     return ap.parse_args()
 
 
@@ -694,6 +696,97 @@ def run_gsweep(args):
                           "clocks": clk.summary(), "sweep": rows}), flush=True)
 
 
+def run_proposal(args):
+    """The learned-proposal family: an MLP (O3, FP64, trained on the host on a
+    sample of training seed 1, labelled with the groups of that seed's final
+    centroids) seeds iteration 0 of held-out seed 9; fits with and without it."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from oracle import mlp
+    from paper_1905_09345_gb300 import kpynq, synth
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    N = args.n or 1 << 23
+    H = 256
+    log = lambda *a: print(*a, file=sys.stderr, flush=True) if rank == 0 else None
+    # training labels: the groups of the final centroids of a fit on seed 1
+    wt = synth.proposal_family(1, N=N)
+    G, K = wt.G, wt.K
+    km = kpynq.KMeans(torch.from_numpy(wt.X).to(dev), torch.from_numpy(wt.C0).to(dev), G, stream=stream)
+    lab = torch.empty(wt.N, dtype=torch.int32, device=dev)
+    km.fit(wt.max_iter, wt.tol, lab, with_stats=False)
+    km.close()
+    grp = (np.arange(K, dtype=np.int64) * G) // K
+    ntrain = min(wt.N, 1 << 16)
+    y = grp[lab[:ntrain].cpu().numpy()]
+    t0 = time.perf_counter()
+    params = mlp.train(wt.X[:ntrain], y, hidden=H, classes=G, seed=1, epochs=args.train_epochs, batch=8192,
+                       lr=1e-3)
+    train_s = time.perf_counter() - t0
+    log(f"[proposal] trained on {ntrain} points x {args.train_epochs} epochs in {train_s:.1f} s")
+    del wt
+    # held-out seed 9
+    w = synth.proposal_family(9, N=N)
+    X = torch.from_numpy(w.X).to(dev)
+    C0 = torch.from_numpy(w.C0).to(dev)
+    lab = torch.empty(w.N, dtype=torch.int32, device=dev)
+    dparams = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in params.items()}
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    with ClockSampler(gpu_uuid()) as clk:
+        for name in ("without", "with"):
+            km = kpynq.KMeans(X, C0, G, stream=stream)
+            if name == "with":
+                km.set_proposal(dparams)
+            times, iters = [], []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                km.reset(C0)
+                r = km.fit(w.max_iter, w.tol, lab, with_stats=False)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+                    iters.append(r.n_iter)
+            st = km.stats(0, iters[-1])
+            prof = kpynq.KMeans(X, C0, G, stream=stream, profile=True)
+            if name == "with":
+                prof.set_proposal(dparams)
+            prof.fit(w.max_iter, w.tol, lab)
+            breakdown = {k: v for k, v in prof.profile().items() if v[0]}
+            prof.close()
+            labels = lab.cpu().numpy()
+            km.close()
+            ms = statistics.mean(times)
+            out[name] = {"ms_per_fit": ms, "iters": iters[-1],
+                         "points_iters_per_s": w.N * statistics.mean(iters) / (ms / 1e3),
+                         "iter0": {k: st[0][k] for k in ("path", "n_dist", "n_survivors", "n_recheck")},
+                         "skip_fraction": 1.0 - sum(s_["n_dist"] for s_ in st) / (w.N * K * len(st)),
+                         "profile_ms": {k: round(v[1], 3) for k, v in breakdown.items()}}
+            if name == "without":
+                final_groups = grp[labels]
+    pred = torch.empty(w.N, dtype=torch.int32, device=dev)
+    kpynq.kmeans_mlp_predict(X, w.N, w.D, *[dparams[k] for k in kpynq.MLP_NAMES], H, G, pred, stream)
+    acc = float((pred.cpu().numpy() == final_groups).mean())
+    if rank != 0:
+        return
+    line = {"metric": "points*iters/s (filtered K-means seeded by the learned proposal, exact labels)",
+            "value": out["with"]["points_iters_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["with"]["ms_per_fit"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "D": w.D, "K": K, "G": G, "hidden": H,
+                       "train": f"O3 (FP64, host) on {ntrain} points of seed 1, {args.train_epochs} epochs, "
+                                f"{train_s:.1f} s", "l2": "flushed between steps"},
+            "clocks": clk.summary(), "proposal_accuracy": acc, "with_proposal": out["with"],
+            "without_proposal": out["without"],
+            "vs_without": out["with"]["points_iters_per_s"] / out["without"]["points_iters_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -702,6 +795,8 @@ def main():
         run_batched(args)
     elif args.workload == "gsweep":
         run_gsweep(args)
+    elif args.workload == "proposal":
+        run_proposal(args)
     else:
         run_ours(args)
 

@@ -128,7 +128,8 @@ enum {
     KM_KERNEL_OTHER = 5,    /* loop control, rebase, bounds export */
     KM_KERNEL_SETTLE = 6,   /* exact settle of the tensor-core pass's near-ties */
     KM_KERNEL_STATS = 7,    /* full recompute of the cluster sums (label sort) */
-    KM_KERNEL_KINDS = 8
+    KM_KERNEL_PROPOSAL = 8, /* the learned proposal: MLP, centroid table, seeded bounds */
+    KM_KERNEL_KINDS = 9
 };
 
 /* kmeans_iter_stats.path */
@@ -335,6 +336,36 @@ KM_API void kmeans_batch_destroy(kmeans_batch *b);
 /* Message of the last failed batch call (b NULL: of the last failed
  * kmeans_batch_init in this thread). */
 KM_API const char *kmeans_batch_last_error(const kmeans_batch *b);
+
+/* Learned group proposal (a layered form on top of the filtered method; the
+ * paper has no learned component).  An MLP  D -> hidden -> hidden -> G  with
+ * GELU activations (the exact erf form) predicts each point's group as the
+ * largest of its G logits.  Weights row-major, output index first:
+ * W1 hidden x D, b1 hidden, W2 hidden x hidden, b2 hidden, W3 G x hidden,
+ * b3 G (FP32, host or device; copied).  With a proposal set, iteration 0 of
+ * the filtered method (KM_ALGO_FILTERED only) replaces its dense pass by:
+ * the prediction; exact FP32 distances to the predicted group's centroids,
+ * giving a label candidate c and u >= d(x, c); group bounds by the triangle
+ * inequality, lb_g = min_{c' in g} d(c, c') - u, from a K x G table of
+ * centroid distances; then the ordinary filtered assignment (global, group
+ * and point filters, distance calculator; Sec. I), so labels are exactly
+ * those without a proposal -- a wrong prediction only costs work.  All six
+ * pointers NULL: remove the proposal.  Allocates the weights, N int32
+ * predictions, two chunk buffers of min(N, 2^20) x hidden floats and the
+ * K x G table.  Errors: KM_EINVAL (Lloyd context, hidden outside [1, 4096],
+ * some pointers NULL), KM_ENOMEM, KM_ECUDA. */
+KM_API int kmeans_set_proposal(kmeans_ctx *c, const float *W1, const float *b1, const float *W2, const float *b2,
+                               const float *W3, const float *b3, int32_t hidden);
+
+/* The proposal MLP alone: pred[n] = argmax_g logits(X[n]) (first maximum)
+ * for N points of dimension D, G classes; weights as above.  X, the weights
+ * and pred are device memory of the current device; ordered on `stream`
+ * (NULL = legacy default), which also holds two temporary chunk buffers
+ * (stream-ordered allocation).  Errors: KM_EINVAL, KM_ECUDA; message in
+ * kmeans_last_error(NULL). */
+KM_API int kmeans_mlp_predict(const float *X, int64_t N, int32_t D, const float *W1, const float *b1,
+                              const float *W2, const float *b2, const float *W3, const float *b3, int32_t hidden,
+                              int32_t classes, int32_t *pred, void *stream);
 
 /* Device self-test of the square-root bounds behind every distance bound
  * (the upper bound u and the lower bounds lb of the filters, Sec. I): the

@@ -43,6 +43,13 @@ struct kmeans_ctx {
     float *X_own = nullptr;
     int tcap = 0;
     bool use_tc = false;   // dense passes on the tensor cores
+    // learned proposal (kmeans_set_proposal): weights W1|b1|W2|b2|W3|b3, the
+    // predictions, two chunk buffers and the centroid-distance table
+    bool proposal = false;
+    int mlp_h = 0;
+    float *mlp = nullptr, *mlp_a1 = nullptr, *mlp_a2 = nullptr, *cc_table = nullptr;
+    int32_t *pred = nullptr;
+    int64_t mlp_chunk = 0;
     bool have_final = false;  // a fit finished: its final-assignment record is kept
     int t_host = 0;        // iterations run (mirrors ctrl->t after each call)
     int v_host = 0;        // table version (mirrors ctrl->v)
@@ -278,15 +285,37 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
         if (e != cudaSuccess) return e;
     }
     // both the survivor kernel and the dense pass append to the moved-point list
-    return enqueue_stats(c, p, s, 0, respect_done);
+    // (a seeded iteration 0 recomputes every cluster sum)
+    return enqueue_stats(c, p, s, first ? 1 : 0, respect_done);
 }
 
 cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {
     return timed(c, s, KM_KERNEL_UPDATE, [&] { return launch_update(p, s, final_only, respect_done); });
 }
 
+// Iteration 0 seeded by the learned proposal: predictions, the centroid
+// table and the seeded bounds (the filtered assignment follows).
+cudaError_t enqueue_proposal(kmeans_ctx *c, const Params &p, cudaStream_t s, int respect_done) {
+    const int H = c->mlp_h, D = p.D, G = p.G;
+    const float *W1 = c->mlp, *b1 = W1 + (size_t)H * D, *W2 = b1 + H, *b2 = W2 + (size_t)H * H, *W3 = b2 + H,
+                *b3 = W3 + (size_t)G * H;
+    return timed(c, s, KM_KERNEL_PROPOSAL, [&] {
+        cudaError_t e = launch_mlp_predict(p.X, p.N, D, W1, b1, W2, b2, W3, b3, H, G, c->pred, c->mlp_a1, c->mlp_a2,
+                                           c->mlp_chunk, s);
+        if (e != cudaSuccess) return e;
+        return launch_proposal_seed(p, c->pred, c->cc_table, s, respect_done, c->num_sms);
+    });
+}
+
 // One full iteration: assignment, then update.
 cudaError_t enqueue_iteration(kmeans_ctx *c, const Params &p, cudaStream_t s, bool first, int respect_done) {
+    if (first && c->proposal && p.algo == KM_ALGO_FILTERED) {
+        cudaError_t e = enqueue_proposal(c, p, s, respect_done);
+        if (e != cudaSuccess) return e;
+        e = enqueue_assign(c, p, s, false, true, respect_done);
+        if (e != cudaSuccess) return e;
+        return enqueue_update(c, p, s, 0, respect_done);
+    }
     const bool dense = first || p.algo == KM_ALGO_LLOYD;
     cudaError_t e = enqueue_assign(c, p, s, dense, first, respect_done);
     if (e != cudaSuccess) return e;
@@ -590,9 +619,10 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.7f : 0.9f);
     if (c->use_tc) {  // the two bfloat16 halves of X, made once
         uint16_t *xh, *xl;
-        INIT_CUDA(dalloc(c, &xh, (size_t)N * D));
-        INIT_CUDA(dalloc(c, &xl, (size_t)N * D));
-        INIT_CUDA(launch_split_x(p.X, N, D, xh, xl, s, c->num_sms));
+        const int Dt = tc_dim(D);  // zero-padded width of the operand copies
+        INIT_CUDA(dalloc(c, &xh, (size_t)N * Dt));
+        INIT_CUDA(dalloc(c, &xl, (size_t)N * Dt));
+        INIT_CUDA(launch_split_x(p.X, N, D, Dt, xh, xl, s, c->num_sms));
         p.Xh = xh;
         p.Xl = xl;
         SettleReq *sq;
@@ -607,8 +637,8 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         p.squeue = sqq;
         if (K > 256) {  // the centroid blocks stream from a split copy made each pass
             const int kp = dense_tcb_kp(p);
-            INIT_CUDA(dalloc(c, &p.Ch, (size_t)kp * D));
-            INIT_CUDA(dalloc(c, &p.Cl, (size_t)kp * D));
+            INIT_CUDA(dalloc(c, &p.Ch, (size_t)kp * Dt));
+            INIT_CUDA(dalloc(c, &p.Cl, (size_t)kp * Dt));
             INIT_CUDA(dalloc(c, &p.cnorm, (size_t)K));
         }
     }
@@ -824,6 +854,79 @@ KM_API void kmeans_destroy(kmeans_ctx *c) {
     if (c->ctrl_host) cudaFreeHost(c->ctrl_host);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
+}
+
+KM_API int kmeans_set_proposal(kmeans_ctx *c, const float *W1, const float *b1, const float *W2, const float *b2,
+                               const float *W3, const float *b3, int32_t hidden) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const bool none = !W1 && !b1 && !W2 && !b2 && !W3 && !b3;
+    if (!none && (!W1 || !b1 || !W2 || !b2 || !W3 || !b3))
+        return set_err(c, KM_EINVAL, "the proposal needs all six weight arrays (or none)");
+    if (!none && c->p.algo != KM_ALGO_FILTERED)
+        return set_err(c, KM_EINVAL, "the proposal seeds the filtered method's bounds (KM_ALGO_FILTERED only)");
+    if (!none && (hidden < 1 || hidden > 4096)) return set_err(c, KM_EINVAL, "hidden=%d outside [1, 4096]", hidden);
+    DeviceGuard dg(c->dev);
+    if ((rc = sync_and_check(c))) return rc;
+    Params &p = c->p;
+    cudaStream_t s = c->stream;
+    if (none) {
+        c->proposal = false;
+    } else {
+        const int D = p.D, G = p.G, H = hidden;
+        const size_t nw = (size_t)H * D + H + (size_t)H * H + H + (size_t)G * H + G;
+        if (H != c->mlp_h) {  // buffers sized for this hidden width (earlier ones stay until destroy)
+            c->mlp_chunk = std::min<int64_t>(p.N, (int64_t)1 << 20);
+            KP_CUDA(c, dalloc(c, &c->mlp, nw));
+            KP_CUDA(c, dalloc(c, &c->mlp_a1, (size_t)c->mlp_chunk * H));
+            KP_CUDA(c, dalloc(c, &c->mlp_a2, (size_t)c->mlp_chunk * H));
+            if (!c->pred) KP_CUDA(c, dalloc(c, &c->pred, (size_t)p.N));
+            if (!c->cc_table) KP_CUDA(c, dalloc(c, &c->cc_table, (size_t)p.K * G));
+            c->mlp_h = H;
+        }
+        const float *src[6] = {W1, b1, W2, b2, W3, b3};
+        const size_t len[6] = {(size_t)H * D, (size_t)H, (size_t)H * H, (size_t)H, (size_t)G * H, (size_t)G};
+        float *dst = c->mlp;
+        for (int i = 0; i < 6; ++i) {
+            KP_CUDA(c, cudaMemcpyAsync(dst, src[i], len[i] * 4, cudaMemcpyDefault, s));
+            dst += len[i];
+        }
+        KP_CUDA(c, cudaStreamSynchronize(s));
+        c->proposal = true;
+    }
+    if (c->graph_exec) {  // recorded with the other iteration 0
+        cudaGraphExecDestroy(c->graph_exec);
+        cudaGraphDestroy(c->graph);
+        c->graph_exec = nullptr;
+        c->graph = nullptr;
+    }
+    return KM_OK;
+}
+
+KM_API int kmeans_mlp_predict(const float *X, int64_t N, int32_t D, const float *W1, const float *b1,
+                              const float *W2, const float *b2, const float *W3, const float *b3, int32_t hidden,
+                              int32_t classes, int32_t *pred, void *stream) {
+    auto fail = [](int code, const char *msg) {
+        set_thread_error(msg);
+        return code;
+    };
+    if (!X || !W1 || !b1 || !W2 || !b2 || !W3 || !b3 || !pred) return fail(KM_EINVAL, "a pointer argument is NULL");
+    if (N < 1 || D < 1 || hidden < 1 || hidden > 4096 || classes < 1)
+        return fail(KM_EINVAL, "N, D, classes >= 1 and hidden in [1, 4096] required");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t chunk = std::min<int64_t>(N, (int64_t)1 << 20);
+    float *a1 = nullptr, *a2 = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&a1), (size_t)chunk * hidden * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&a2), (size_t)chunk * hidden * 4, s);
+    if (e == cudaSuccess)
+        e = launch_mlp_predict(X, N, D, W1, b1, W2, b2, W3, b3, hidden, classes, pred, a1, a2, chunk, s);
+    if (a1) cudaFreeAsync(a1, s);
+    if (a2) cudaFreeAsync(a2, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KM_ECUDA, cudaGetErrorString(e));
+    }
+    return KM_OK;
 }
 
 KM_API const char *kmeans_last_error(const kmeans_ctx *c) { return c ? c->err : g_init_error; }

@@ -332,12 +332,21 @@ int dense_dp(int D);  // register tile width used for D (0 = generic path)
 // `if_dense`: run only when the filter kernel chose the dense pass for this iteration
 cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                                 int if_dense = 0);
+// Width of the bfloat16 operand copies of the tensor-core passes: rows of 32
+// coordinates are zero-padded to 64 (the padding adds exact zeros to every
+// product); 0 = no tensor-core pass for this D.
+__host__ __device__ inline int tc_dim(int D) { return D == 32 || D == 64 ? 64 : (D == 128 ? 128 : 0); }
 bool dense_tc_eligible(const Params &p, size_t smem_limit);
 bool dense_tcb_eligible(const Params &p, size_t smem_limit);
+cudaError_t launch_mlp_predict(const float *X, int64_t N, int D, const float *W1, const float *b1, const float *W2,
+                               const float *b2, const float *W3, const float *b3, int H, int G, int32_t *pred,
+                               float *A1, float *A2, int64_t chunk, cudaStream_t s);
+cudaError_t launch_proposal_seed(const Params &p, const int32_t *pred, float *T, cudaStream_t s, int respect_done,
+                                 int num_sms);
 int dense_tcb_kp(const Params &p);  // padded K of the split centroid copy
 cudaError_t launch_dense_tcb(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                              size_t smem_limit, int if_dense);
-cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
+cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
                            int num_sms);
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int idx = threadIdx.x; idx < Kp * (D / 8); idx += blockDim.x) {
         const int row = idx / (D / 8), q = idx - row * (D / 8);
         float vals[8];
-        if (row < K) {
+        if (row < K && q * 8 < p.D) {  // coordinates beyond D: zero padding
             const float4 a = *reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp + q * 8);
             const float4 b = *reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp + q * 8 + 4);
             vals[0] = a.x; vals[1] = a.y; vals[2] = a.z; vals[3] = a.w;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (k < K) {
                 const float *c = p.C + (size_t)k * p.Dp;
                 float a0 = 0.f, a1 = 0.f;
-                for (int d = 0; d + 1 < D; d += 2) {
+                for (int d = 0; d + 1 < p.D; d += 2) {
                     a0 = fmaf(c[d], c[d], a0);
                     a1 = fmaf(c[d + 1], c[d + 1], a1);
                 }
@@ -889,10 +889,15 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle_t(Params p, int fi
     }
 }
 
-// X -> (x_h, x_l) bfloat16 copies, four elements per thread
-__global__ void k_split_x(const float *X, int64_t n4, uint2 *Xh, uint2 *Xl) {
+// X -> (x_h, x_l) bfloat16 copies with rows of Dt >= D coordinates (zero
+// padding), four elements per thread
+__global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, uint2 *Xl) {
+    const int q4n = Dt / 4;
+    const int64_t n4 = N * q4n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 a = reinterpret_cast<const float4 *>(X)[i];
+        const int64_t row = i / q4n;
+        const int q4 = (int)(i - row * q4n);
+        const float4 a = q4 * 4 < D ? *reinterpret_cast<const float4 *>(X + row * D + q4 * 4) : make_float4(0, 0, 0, 0);
         const float vv[4] = {a.x, a.y, a.z, a.w};
         uint32_t hw[2], lw[2];
 #pragma unroll
@@ -915,12 +920,13 @@ int pow2_at_least(int x) {
 }
 
 bool plan(const Params &p, size_t smem_limit, TcCfg &cfg, size_t &smem) {
-    if (p.D % 64 != 0 || p.D > 128 || p.K > 256) return false;
+    const int Dt = tc_dim(p.D);
+    if (!Dt || p.K > 256) return false;
     cfg.Kp = ((p.K + 31) / 32) * 32;
     cfg.buf_cols = pow2_at_least(cfg.Kp);
     cfg.tmem_cols = kGroups * cfg.buf_cols;
     if (cfg.tmem_cols > 512) return false;
-    const size_t NA = p.D / 64;
+    const size_t NA = Dt / 64;
     const size_t b_bytes = 2 * NA * (size_t)cfg.Kp * 128;
     const size_t a_stage = 2 * NA * (size_t)kAtomBytes;
     const size_t cn_bytes = (size_t)cfg.Kp * 8;  // norms and group-opening penalties
@@ -944,7 +950,7 @@ bool plan(const Params &p, size_t smem_limit, TcCfg &cfg, size_t &smem) {
     smem = 1024 + off;
     if (smem > smem_limit) return false;
     cfg.num_tiles = (int)((p.N + kTM - 1) / kTM);
-    const double D = p.D;
+    const double D = Dt;  // the padded width: its zero products add nothing, the bound stays valid
     cfg.e_lin = (float)(1.25 * (6.1 * std::ldexp(1.0, -16) + (6 * D + 1) * std::ldexp(1.0, -23)) * (1 + 1e-6));
     cfg.e_c2 = (float)(1.25 * (D + 3) * std::ldexp(1.0, -24) * (1 + 1e-6));
     // ||x||^2 from x_h + x_l: (1 +- 2^-16)^2 per element and an FP32 sum of D squares
@@ -963,7 +969,8 @@ cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_don
     auto enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tmh, tml;
-    cuuint64_t gx[2] = {(cuuint64_t)p.D, (cuuint64_t)p.N}, sx[1] = {(cuuint64_t)p.D * 2};
+    const int Dt = tc_dim(p.D);
+    cuuint64_t gx[2] = {(cuuint64_t)Dt, (cuuint64_t)p.N}, sx[1] = {(cuuint64_t)Dt * 2};
     cuuint32_t bx[2] = {64, (cuuint32_t)kTM}, es[2] = {1, 1};
     if (enc(&tmh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(p.Xh), gx, sx, bx, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -984,7 +991,7 @@ cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_don
 }  // namespace
 
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms) {
-    if (p.D != 64 && p.D != 128) return cudaErrorInvalidValue;
+    if (p.D != 32 && p.D != 64 && p.D != 128) return cudaErrorInvalidValue;
     // compact the request bitmap (one warp per 32 words), then one thread per request
     const int64_t words = (p.N + 31) / 32;
     const int64_t gblocks = std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, (int64_t)num_sms * 8));
@@ -996,10 +1003,11 @@ cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respec
     // rows with C in shared memory: thread per request (C rows padded by 4
     // floats), else sub-warps (C rows unpadded)
     const int staged = (size_t)p.K * (p.D + 4) * 4 <= ((size_t)160 << 10);
-    const bool per_thread = staged && p.D == 64;
+    const bool per_thread = staged && p.D <= 64;
     const size_t cbytes = staged ? (size_t)p.K * (p.D + (per_thread ? 4 : 0)) * 4 : 0;
     const size_t smem = cbytes + (size_t)(p.G + 1) * 4;
-    auto kern = per_thread ? k_settle_t<64> : (p.D == 64 ? k_settle<64> : k_settle<128>);
+    auto kern = per_thread ? (p.D == 32 ? k_settle_t<32> : k_settle_t<64>)
+                           : (p.D == 32 ? k_settle<32> : (p.D == 64 ? k_settle<64> : k_settle<128>));
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1016,12 +1024,12 @@ bool dense_tc_eligible(const Params &p, size_t smem_limit) {
     return encoder() != nullptr && plan(p, smem_limit, cfg, smem);
 }
 
-cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
+cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
                            int num_sms) {
-    const int64_t n4 = N * D / 4;  // D is a multiple of 64
+    const int64_t n4 = N * Dt / 4;  // D and Dt are multiples of 4
     const int64_t grid = std::min<int64_t>((n4 + 255) / 256, (int64_t)num_sms * 16);
     count_launch();
-    k_split_x<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(X, n4, reinterpret_cast<uint2 *>(Xh),
+    k_split_x<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(X, N, D, Dt, reinterpret_cast<uint2 *>(Xh),
                                                                     reinterpret_cast<uint2 *>(Xl));
     return cudaGetLastError();
 }
@@ -1029,7 +1037,7 @@ cudaError_t launch_split_x(const float *X, int64_t N, int D, uint16_t *Xh, uint1
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense) {
     if (p.K > 256) return launch_dense_tcb(p, s, first, respect_done, num_sms, smem_limit, if_dense);
-    switch (p.D) {
+    switch (tc_dim(p.D)) {
     case 64: return launch_t<64>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
     case 128: return launch_t<128>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
     default: return cudaErrorNotSupported;

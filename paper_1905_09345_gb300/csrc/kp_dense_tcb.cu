@@ -397,11 +397,11 @@ __global__ void k_split_c(Params p, int Kp, int respect_done, int if_dense) {
     count_kernel(ctrl);
     if (respect_done && *(volatile int *)&ctrl->done) return;
     if (if_dense && !*(volatile int *)&ctrl->dense_mode) return;
-    const int D = p.D;
-    const int64_t total = (int64_t)Kp * D;
+    const int D = p.D, Dt = tc_dim(p.D);
+    const int64_t total = (int64_t)Kp * Dt;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i / D), d = (int)(i - (int64_t)k * D);
-        const float x = k < p.K ? p.C[(size_t)k * p.Dp + d] : 0.f;
+        const int k = (int)(i / Dt), d = (int)(i - (int64_t)k * Dt);
+        const float x = (k < p.K && d < D) ? p.C[(size_t)k * p.Dp + d] : 0.f;  // zero padding
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
         const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
         p.Ch[i] = __bfloat16_as_ushort(h);
@@ -426,7 +426,8 @@ __global__ void k_split_c(Params p, int Kp, int respect_done, int if_dense) {
 }
 
 bool plan_b(const Params &p, size_t smem_limit, TcbCfg &cfg, size_t &smem) {
-    if (p.D % 64 != 0 || p.D > 128 || p.K <= 256 || p.algo != KM_ALGO_FILTERED) return false;
+    const int Dt = tc_dim(p.D);
+    if (!Dt || p.K <= 256 || p.algo != KM_ALGO_FILTERED) return false;
     cfg.Kp = ((p.K + kNB - 1) / kNB) * kNB;
     if (cfg.Kp > kMaxKp) return false;
     cfg.nb = cfg.Kp / kNB;
@@ -441,7 +442,7 @@ bool plan_b(const Params &p, size_t smem_limit, TcbCfg &cfg, size_t &smem) {
         most = std::max(most, g1 - g0 + 1);
     }
     cfg.srow = (most + 2) | 1;
-    const size_t NA = p.D / 64;
+    const size_t NA = Dt / 64;
     const size_t a_stage = 2 * NA * (size_t)kAtomBytes;
     const size_t b_stage = 2 * NA * (size_t)kBAtom;
     const size_t tables = (size_t)cfg.Kp * 8 + (size_t)cfg.Kp / 32 * 4;
@@ -467,7 +468,7 @@ bool plan_b(const Params &p, size_t smem_limit, TcbCfg &cfg, size_t &smem) {
     smem = 1024 + off;
     if (smem > smem_limit) return false;
     cfg.num_tiles = (int)((p.N + kTM - 1) / kTM);
-    const double D = p.D;
+    const double D = Dt;  // the padded width (zero products add nothing)
     cfg.e_lin = (float)(1.25 * (6.1 * std::ldexp(1.0, -16) + (6 * D + 1) * std::ldexp(1.0, -23)) * (1 + 1e-6));
     cfg.e_c2 = (float)(1.25 * (D + 3) * std::ldexp(1.0, -24) * (1 + 1e-6));
     const double rel = 2 * (std::ldexp(1.0, -15) + (D + 2) * std::ldexp(1.0, -24));
@@ -486,8 +487,9 @@ cudaError_t launch_b(const Params &p, cudaStream_t s, int first, int respect_don
     auto enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tmh, tml, tmch, tmcl;
-    cuuint64_t gx[2] = {(cuuint64_t)p.D, (cuuint64_t)p.N}, sx[1] = {(cuuint64_t)p.D * 2};
-    cuuint64_t gc[2] = {(cuuint64_t)p.D, (cuuint64_t)cfg.Kp};
+    const int Dt = tc_dim(p.D);
+    cuuint64_t gx[2] = {(cuuint64_t)Dt, (cuuint64_t)p.N}, sx[1] = {(cuuint64_t)Dt * 2};
+    cuuint64_t gc[2] = {(cuuint64_t)Dt, (cuuint64_t)cfg.Kp};
     cuuint32_t bx[2] = {64, (cuuint32_t)kTM}, bc[2] = {64, (cuuint32_t)kNB}, es[2] = {1, 1};
     struct M {
         CUtensorMap *m;
@@ -501,7 +503,7 @@ cudaError_t launch_b(const Params &p, cudaStream_t s, int first, int respect_don
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     {
-        const int64_t total = (int64_t)cfg.Kp * p.D;
+        const int64_t total = (int64_t)cfg.Kp * Dt;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 4));
         count_launch();
         k_split_c<<<(unsigned)grid, 256, 0, s>>>(p, cfg.Kp, respect_done, if_dense);
@@ -528,7 +530,7 @@ int dense_tcb_kp(const Params &p) { return ((p.K + kNB - 1) / kNB) * kNB; }
 
 cudaError_t launch_dense_tcb(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                              size_t smem_limit, int if_dense) {
-    switch (p.D) {
+    switch (tc_dim(p.D)) {
     case 64: return launch_b<64>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
     case 128: return launch_b<128>(p, s, first, respect_done, num_sms, smem_limit, if_dense);
     default: return cudaErrorNotSupported;

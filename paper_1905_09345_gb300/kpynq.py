@@ -22,8 +22,9 @@ KM_GROUP_CONTIGUOUS = 0
 KM_DENSE_AUTO, KM_DENSE_FP32 = 0, 1
 KM_PATH_FILTERED, KM_PATH_DENSE_FP32, KM_PATH_DENSE_TC = 0, 1, 2
 (KM_KERNEL_DENSE, KM_KERNEL_MOVES, KM_KERNEL_FILTER, KM_KERNEL_SURVIVOR, KM_KERNEL_UPDATE, KM_KERNEL_OTHER,
- KM_KERNEL_SETTLE, KM_KERNEL_STATS) = range(8)
-KERNEL_KIND_NAMES = ["dense_assign", "apply_moves", "filter", "survivor", "update", "other", "settle", "stats"]
+ KM_KERNEL_SETTLE, KM_KERNEL_STATS, KM_KERNEL_PROPOSAL) = range(9)
+KERNEL_KIND_NAMES = ["dense_assign", "apply_moves", "filter", "survivor", "update", "other", "settle", "stats",
+                     "proposal"]
 STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ENOMEM", -3: "KM_ECUDA", -4: "KM_ETIMEOUT",
                 -5: "KM_ESTATE"}
 
@@ -71,6 +72,10 @@ def lib():
         L.kmeans_default_options.argtypes = [ctypes.POINTER(kmeans_options)]
         L.kmeans_default_options.restype = None
         L.kmeans_selftest_sqrt.argtypes = [ctypes.POINTER(i64)]
+        L.kmeans_set_proposal.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32]
+        L.kmeans_set_proposal.restype = ctypes.c_int
+        L.kmeans_mlp_predict.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        L.kmeans_mlp_predict.restype = ctypes.c_int
         L.kmeans_selftest_sqrt.restype = ctypes.c_int
         L.kmeans_init.argtypes = [ctypes.POINTER(vp), vp, i64, i32, i32, i32, vp, ctypes.POINTER(kmeans_options)]
         L.kmeans_init.restype = ctypes.c_int
@@ -169,6 +174,23 @@ def kmeans_selftest_sqrt() -> int:
     v = ctypes.c_int64(-1)
     _check(lib().kmeans_selftest_sqrt(ctypes.byref(v)), None)
     return v.value
+
+
+MLP_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def kmeans_set_proposal(ctx, W1, b1, W2, b2, W3, b3, hidden: int) -> None:
+    """Set (or, with all six None, remove) the learned group proposal."""
+    _check(lib().kmeans_set_proposal(ctx, _addr(W1), _addr(b1), _addr(W2), _addr(b2), _addr(W3), _addr(b3),
+                                     hidden), ctx)
+
+
+def kmeans_mlp_predict(X, N: int, D: int, W1, b1, W2, b2, W3, b3, hidden: int, classes: int, pred,
+                       stream=None) -> None:
+    """The proposal MLP's argmax group for every point (device arrays)."""
+    st = stream if isinstance(stream, int) or stream is None else stream.cuda_stream
+    _check(lib().kmeans_mlp_predict(_addr(X), N, D, _addr(W1), _addr(b1), _addr(W2), _addr(b2), _addr(W3),
+                                    _addr(b3), hidden, classes, _addr(pred), st), None)
 
 
 def kmeans_init(X, N: int, D: int, K: int, G: int, init_centroids, opt: kmeans_options | None = None):
@@ -299,6 +321,17 @@ class KMeans:
         self._keep = (X, C0)
         self.N, self.D, self.K, self.G = N, D, K, G
         self.ctx = kmeans_init(X, N, D, K, G, C0, opt)
+
+    def set_proposal(self, params: dict | None):
+        """params: {"W1", "b1", "W2", "b2", "W3", "b3"} FP32 arrays (host or
+        device), or None to remove the proposal."""
+        if params is None:
+            kmeans_set_proposal(self.ctx, None, None, None, None, None, None, 0)
+            self._proposal = None
+            return
+        w = [params[k] for k in MLP_NAMES]
+        self._proposal = w  # keep the arrays alive until the copy has been made
+        kmeans_set_proposal(self.ctx, *w, int(w[0].shape[0]))
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -52,7 +52,8 @@ def tc_expected(D, K, G, smem=232448, algo=0):
     """Mirror of the tensor-core kernels' eligibility (shape and shared memory):
     one accumulator block for K <= 256, streamed centroid blocks above (the
     filtered method only)."""
-    if D % 64 or D > 128:
+    Dt = {32: 64, 64: 64, 128: 128}.get(D)  # operand copies zero-padded to 64 / 128
+    if Dt is None:
         return False
     if K > 256:
         if algo != 0:
@@ -67,7 +68,7 @@ def tc_expected(D, K, G, smem=232448, algo=0):
                 break
             most = max(most, c1 * G // K - c0 * G // K + 1)
         srow = (most + 2) | 1
-        na = D // 64
+        na = Dt // 64
         a_stage = b_stage = 2 * na * 128 * 128
         stage = 2 * 4 * 32 * srow * 4
         for bst in (2, 1):
@@ -77,7 +78,7 @@ def tc_expected(D, K, G, smem=232448, algo=0):
                 return True
         return False
     Kp = (K + 31) // 32 * 32
-    na = D // 64
+    na = Dt // 64
     Gp = (G + 3) // 4 * 4
     fixed = 1024 + 2 * na * Kp * 128 + Kp * 4 + ((G + 1) * 4 + 15) // 16 * 16 + 2 * 128 * (Gp + 1) * 4 + 64 * 8 + 64
     return fixed + 2 * 2 * na * 128 * 128 <= smem
@@ -450,6 +451,7 @@ KBLOCKED = [
     (100003, 128, 520, 100, 3),
     (20000, 64, 1024, 103, 3),
     (5000, 128, 257, 1, 3),
+    (30000, 32, 600, 60, 3),   # 32 coordinates, zero-padded to 64 in the operand copies
 ]
 
 
