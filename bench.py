@@ -222,7 +222,9 @@ def algorithmic(kind: str, w, stats: list, launches: int) -> list[tuple[str, flo
     larger fraction of its peak."""
     N, D, K, G = w.N, w.D, w.K, w.G
     Gp = (G + 3) // 4 * 4
-    filt = [s for s in stats if s["iter"] > 0]
+    # the filtered iterations proper: the survivor kernel does no work in
+    # iterations that switched to the dense pass (path != 0)
+    filt = [s for s in stats if s["iter"] > 0 and s["path"] == 0]
     dense_fp32 = [s for s in stats if s["path"] == 1]
     mean = lambda key, rows: sum(s[key] for s in rows) / max(1, len(rows))
     if kind == "dense_assign":

@@ -215,28 +215,27 @@ struct WarpScratch {
 
 template <int DP>
 __device__ __forceinline__ float sqdist_lane(const float *__restrict__ xs, const float *__restrict__ c, int D) {
-    float a0 = 0.f, a1 = 0.f;
     if constexpr (DP > 0) {
+        // packed FP32x2 subtract / fused multiply-add (each half an ordinary
+        // round-to-nearest FP32 operation): half the instructions of the
+        // scalar form; four partial sums of DP/4 terms
+        unsigned long long a0 = 0ull, a1 = 0ull;
 #pragma unroll
-        for (int i = 0; i < DP; i += 8) {
-            float4 x0 = *reinterpret_cast<const float4 *>(xs + i);
-            float4 c0 = *reinterpret_cast<const float4 *>(c + i);
-            float t0 = x0.x - c0.x, t1 = x0.y - c0.y, t2 = x0.z - c0.z, t3 = x0.w - c0.w;
-            a0 = fmaf(t0, t0, a0);
-            a0 = fmaf(t1, t1, a0);
-            a0 = fmaf(t2, t2, a0);
-            a0 = fmaf(t3, t3, a0);
-            if (i + 4 < DP) {
-                float4 x1 = *reinterpret_cast<const float4 *>(xs + i + 4);
-                float4 c1 = *reinterpret_cast<const float4 *>(c + i + 4);
-                float u0 = x1.x - c1.x, u1 = x1.y - c1.y, u2 = x1.z - c1.z, u3 = x1.w - c1.w;
-                a1 = fmaf(u0, u0, a1);
-                a1 = fmaf(u1, u1, a1);
-                a1 = fmaf(u2, u2, a1);
-                a1 = fmaf(u3, u3, a1);
-            }
+        for (int i = 0; i < DP; i += 4) {
+            const ulonglong2 x2 = *reinterpret_cast<const ulonglong2 *>(xs + i);
+            const ulonglong2 c2 = *reinterpret_cast<const ulonglong2 *>(c + i);
+            unsigned long long d0, d1;
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(x2.x), "l"(c2.x));
+            asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(x2.y), "l"(c2.y));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
+            asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
         }
+        float l0, h0, l1, h1;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(l0), "=f"(h0) : "l"(a0));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(l1), "=f"(h1) : "l"(a1));
+        return (l0 + h0) + (l1 + h1);
     } else {
+        float a0 = 0.f, a1 = 0.f;
         int i = 0;
         for (; i + 1 < D; i += 2) {
             float t0 = xs[i] - c[i], t1 = xs[i + 1] - c[i + 1];
@@ -247,8 +246,8 @@ __device__ __forceinline__ float sqdist_lane(const float *__restrict__ xs, const
             float t0 = xs[i] - c[i];
             a0 = fmaf(t0, t0, a0);
         }
+        return a0 + a1;
     }
-    return a0 + a1;
 }
 
 // point-filter bound of centroid c (group g) for a point stamped at version w
