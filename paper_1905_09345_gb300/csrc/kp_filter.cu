@@ -256,7 +256,7 @@ __device__ __forceinline__ float point_bound(const Params &p, float lb_stored, i
 }
 
 template <int DP, bool STAGE>
-__global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, int warps_per_block) {
+__global__ void __launch_bounds__(512, 2) k_survivor(Params p, int respect_done, int warps_per_block) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     Ctrl *ctrl = p.ctrl;
@@ -291,17 +291,60 @@ __global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, in
 
     unsigned long long c_scanned = 0, c_dist = 0, c_recheck = 0, c_changed = 0, c_dist_lane = 0;
 
+    // The next point's id, label, stamp, global bound, coordinates and (up
+    // to 128 groups) bound row are loaded while the current one is processed:
+    // each point's loads otherwise form a chain of dependent global reads.
+    constexpr int XPL = DP > 0 ? (DP + 31) / 32 : 1;  // coordinates per lane
+    constexpr int LPL = 4;                           // bound-row entries per lane
+    const bool pf_lb = DP > 0 && G <= 32 * LPL;
+    int64_t pn = 0;
+    int pa = 0;
+    uint32_t pst = 0;
+    float plbg = 0.f, px[XPL], plb[LPL];
+    auto prefetch = [&](int idx) {
+        if (idx >= count) return;  // warp-uniform
+        pn = p.queue[idx];
+        pa = p.label[pn];
+        pst = p.stamp[pn];
+        plbg = p.lbg[pn];
+        if constexpr (DP > 0) {
+#pragma unroll
+            for (int k = 0; k < XPL; ++k) {
+                const int i = lane + 32 * k;
+                px[k] = i < D ? __ldg(p.X + pn * D + i) : 0.f;
+            }
+        }
+        if (pf_lb) {
+#pragma unroll
+            for (int k = 0; k < LPL; ++k) {
+                const int g = lane + 32 * k;
+                plb[k] = g < G ? p.lb[pn * p.Gp + g] : 0.f;
+            }
+        }
+    };
+    prefetch(gwarp);
+
     for (int it = gwarp; it < count; it += nwarps) {
-        const int64_t n = p.queue[it];
-        const int a = p.label[n];
-        const uint32_t st = p.stamp[n];
+        const int64_t n = pn;
+        const int a = pa;
+        const uint32_t st = pst;
         const int wu = (int)stamp_u(st), wl = (int)stamp_l(st);
-        const float lbg_e = __fsub_rd(p.lbg[n], drift_m(p, v, wl));
+        const float lbg_e = __fsub_rd(plbg, drift_m(p, v, wl));
+        float clb[LPL];
+#pragma unroll
+        for (int k = 0; k < LPL; ++k) clb[k] = plb[k];
 
         // the point
-        const float *xg = p.X + n * D;
-        for (int i = lane; i < DPa; i += 32) xs[i] = i < D ? __ldg(xg + i) : 0.f;
+        if constexpr (DP > 0) {
+#pragma unroll
+            for (int k = 0; k < XPL; ++k)
+                if (lane + 32 * k < DPa) xs[lane + 32 * k] = px[k];
+        } else {
+            const float *xg = p.X + n * D;
+            for (int i = lane; i < DPa; i += 32) xs[i] = i < D ? __ldg(xg + i) : 0.f;
+        }
         __syncwarp();
+        prefetch(it + nwarps);
 
         // tighten: exact distance to the own centroid (lanes split the
         // coordinates; any summation order is covered by the error bound)
@@ -331,7 +374,15 @@ __global__ void __launch_bounds__(512) k_survivor(Params p, int respect_done, in
             bool surv = false;
             int size = 0;
             if (g < G) {
-                float lr = p.lb[n * p.Gp + g];
+                float lr;
+                if (pf_lb) {  // prefetched: entry g0 / 32 of this lane
+                    lr = clb[0];
+#pragma unroll
+                    for (int k = 1; k < LPL; ++k)
+                        if ((g0 >> 5) == k) lr = clb[k];
+                } else {
+                    lr = p.lb[n * p.Gp + g];
+                }
                 float le = __fsub_rd(lr, drift_g(p, v, wl, g));
                 lbr[g] = lr;
                 lbe[g] = le;
