@@ -115,6 +115,15 @@ def test_null_context_calls(L):
     assert lib.kmeans_fit(None, 1, 0.0, None, None, None, None) == L.KM_EINVAL
     lib.kmeans_destroy(None)
     assert L.kmeans_launch_count() >= 0
+    # the proposal entry points reject bad arguments before any device work
+    assert lib.kmeans_set_proposal(None, None, None, None, None, None, None, 0) == L.KM_EINVAL
+    assert lib.kmeans_mlp_predict(None, 10, 4, None, None, None, None, None, None, 8, 3, None, None) == L.KM_EINVAL
+    fake = 16  # any non-NULL address: the size checks come first
+    assert lib.kmeans_mlp_predict(fake, 0, 4, fake, fake, fake, fake, fake, fake, 8, 3, fake, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_predict(fake, 10, 4, fake, fake, fake, fake, fake, fake, 5000, 3, fake, None) == L.KM_EINVAL
+    assert "hidden" in L.kmeans_last_error(None)
+    lib.kmeans_selftest_sqrt.restype = __import__("ctypes").c_int
+    assert lib.kmeans_selftest_sqrt(None) == L.KM_EINVAL
 
 
 def test_default_options(L):
