@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -118,10 +119,45 @@ bool is_device_ptr(const void *ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Every context allocates from one library-owned memory pool per device
+// (stream-ordered, on the context's stream; everything a context allocates is
+// used on that stream or after a synchronisation).  Freed blocks stay in the
+// pool up to 32 GiB, so that contexts made one after another -- a job that
+// creates a context per data set -- reuse memory instead of paying
+// cudaMalloc / cudaFree each time.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[256] = {};
+
+cudaError_t lib_pool(int dev, cudaMemPool_t *out) {
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = (uint64_t)32 << 30;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
 template <class T>
 cudaError_t dalloc(kmeans_ctx *c, T **p, size_t count) {
+    cudaMemPool_t pool;
+    cudaError_t e = lib_pool(c->dev, &pool);
+    if (e != cudaSuccess) return e;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    e = cudaMallocFromPoolAsync(&q, count * sizeof(T) + 16, pool, c->stream);
     if (e != cudaSuccess) return e;
     c->allocs.push_back(q);
     *p = static_cast<T *>(q);
@@ -850,7 +886,8 @@ KM_API void kmeans_destroy(kmeans_ctx *c) {
         c->ev_pool.push_back(q.b);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    for (void *q : c->allocs) cudaFree(q);
+    for (void *q : c->allocs) cudaFreeAsync(q, c->stream);
+    cudaStreamSynchronize(c->stream);
     if (c->ctrl_host) cudaFreeHost(c->ctrl_host);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
