@@ -555,6 +555,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
 
     // X: borrowed when FP32 on the device, copied otherwise (bfloat16: an
     // exact FP32 copy)
+    const float *x_host_dev = nullptr;  // host X readable by the device (copied later)
     if (o.dtype == KM_DTYPE_BF16) {
         INIT_CUDA(dalloc(c, &c->X_own, (size_t)N * D));
         const uint16_t *xb = reinterpret_cast<const uint16_t *>(X);
@@ -571,7 +572,15 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         p.X = X;
     } else {
         INIT_CUDA(dalloc(c, &c->X_own, (size_t)N * D));
-        INIT_CUDA(cudaMemcpyAsync(c->X_own, X, (size_t)N * D * 4, cudaMemcpyDefault, c->stream));
+        // page-locked host memory the device can read: the tensor-core
+        // split below copies and splits in one pass over it; otherwise copy
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, X) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer &&
+            D % 4 == 0 && (reinterpret_cast<uintptr_t>(pa.devicePointer) & 15) == 0)
+            x_host_dev = static_cast<const float *>(pa.devicePointer);
+        else
+            INIT_CUDA(cudaMemcpyAsync(c->X_own, X, (size_t)N * D * 4, cudaMemcpyDefault, c->stream));
+        cudaGetLastError();
         p.X = c->X_own;
     }
     p.x_vec4 = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.X) & 15) == 0);
@@ -658,7 +667,10 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         const int Dt = tc_dim(D);  // zero-padded width of the operand copies
         INIT_CUDA(dalloc(c, &xh, (size_t)N * Dt));
         INIT_CUDA(dalloc(c, &xl, (size_t)N * Dt));
-        INIT_CUDA(launch_split_x(p.X, N, D, Dt, xh, xl, s, c->num_sms));
+        // from the host copy when X is still there (the FP32 copy is made in the same pass)
+        INIT_CUDA(launch_split_x(x_host_dev ? x_host_dev : p.X, N, D, Dt, xh, xl, s, c->num_sms,
+                                 x_host_dev ? c->X_own : nullptr));
+        x_host_dev = nullptr;
         p.Xh = xh;
         p.Xl = xl;
         SettleReq *sq;
@@ -679,6 +691,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         }
     }
 
+    if (x_host_dev) INIT_CUDA(cudaMemcpyAsync(c->X_own, X, (size_t)N * D * 4, cudaMemcpyDefault, s));
     if (o.validate) {
         INIT_CUDA(cudaMemsetAsync(c->flag_dev, 0, 4, s));
         INIT_CUDA(launch_check_finite(p.X, N * D, c->flag_dev, s, c->num_sms));

@@ -347,7 +347,7 @@ int dense_tcb_kp(const Params &p);  // padded K of the split centroid copy
 cudaError_t launch_dense_tcb(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                              size_t smem_limit, int if_dense);
 cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
-                           int num_sms);
+                           int num_sms, float *Xcopy = nullptr);
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);

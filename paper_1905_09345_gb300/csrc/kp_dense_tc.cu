@@ -891,13 +891,14 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle_t(Params p, int fi
 
 // X -> (x_h, x_l) bfloat16 copies with rows of Dt >= D coordinates (zero
 // padding), four elements per thread
-__global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, uint2 *Xl) {
+__global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, uint2 *Xl, float4 *Xcopy) {
     const int q4n = Dt / 4;
     const int64_t n4 = N * q4n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = i / q4n;
         const int q4 = (int)(i - row * q4n);
         const float4 a = q4 * 4 < D ? *reinterpret_cast<const float4 *>(X + row * D + q4 * 4) : make_float4(0, 0, 0, 0);
+        if (Xcopy && q4 * 4 < D) Xcopy[(row * D + q4 * 4) / 4] = a;  // the device copy, in the same pass
         const float vv[4] = {a.x, a.y, a.z, a.w};
         uint32_t hw[2], lw[2];
 #pragma unroll
@@ -1025,12 +1026,13 @@ bool dense_tc_eligible(const Params &p, size_t smem_limit) {
 }
 
 cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
-                           int num_sms) {
+                           int num_sms, float *Xcopy) {
     const int64_t n4 = N * Dt / 4;  // D and Dt are multiples of 4
     const int64_t grid = std::min<int64_t>((n4 + 255) / 256, (int64_t)num_sms * 16);
     count_launch();
     k_split_x<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(X, N, D, Dt, reinterpret_cast<uint2 *>(Xh),
-                                                                    reinterpret_cast<uint2 *>(Xl));
+                                                                    reinterpret_cast<uint2 *>(Xl),
+                                                                    reinterpret_cast<float4 *>(Xcopy));
     return cudaGetLastError();
 }
 

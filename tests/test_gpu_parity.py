@@ -489,3 +489,23 @@ def test_kblocked_matches_fp32_engine_and_near_ties(kp):
     assert outs[0][0] == outs[1][0]
     assert np.array_equal(outs[0][1], outs[1][1])
     assert abs(outs[0][2] - outs[1][2]) <= 1e-9 * outs[1][2]
+
+
+@pytest.mark.parametrize("D,K", [(64, 48), (32, 300), (17, 20)], ids=["tc", "tc_streamed", "fp32"])
+def test_pinned_host_input_matches_device(kp, D, K):
+    """Page-locked host X: the tensor-core split reads it directly and makes the
+    device copy in the same pass; the fit must equal the one from device X."""
+    rng = np.random.default_rng(D + K)
+    N = 7001
+    X, _ = synth.gaussian_mixture(rng, N, D, K, centre_range=10.0, scale="fixed", scale_args=(1.0,))
+    C0 = synth.sample_init(rng, X, K)
+    outs = []
+    for src in (torch.from_numpy(X).cuda(), torch.from_numpy(X).pin_memory()):
+        km = kp.KMeans(src, torch.from_numpy(C0).cuda(), max(1, K // 10))
+        lab = torch.empty(N, dtype=torch.int32, device="cuda")
+        r = km.fit(10, 0.0, lab)
+        outs.append((r.n_iter, lab.cpu().numpy(), r.objective))
+        km.close()
+    assert outs[0][0] == outs[1][0]
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert abs(outs[0][2] - outs[1][2]) <= 1e-9 * outs[0][2]
