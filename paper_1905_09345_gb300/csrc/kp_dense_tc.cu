@@ -39,9 +39,23 @@ namespace kp {
 
 namespace {
 
-constexpr int kEpiWarps = 4;      // warps per epilogue group
+constexpr int kEpiWarps = 8;      // warps per epilogue group: two per TMEM lane quadrant
 constexpr int kGroups = 2;        // epilogue groups = TMEM buffers
 constexpr int kTcThreads = 64 + kGroups * kEpiWarps * 32;
+
+// the two warps of a quadrant (named barrier `id`, 64 threads): every thread
+// contributes v, every thread gets the AND
+__device__ __forceinline__ bool pair_and(bool v, int id) {
+    int out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.and.pred q, %2, 64, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"((int)v), "r"(id)
+        : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
 
 struct TcCfg {
     int Kp;        // centroid rows in shared memory (multiple of 32, <= 256)
@@ -75,7 +89,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float *cn = reinterpret_cast<float *>(sm + cfg.off_cn);  // [Kp] ||c||^2 (+inf: padding)
     float *pen = cn + Kp;  // [Kp] +inf where a group opens, else 0
     uint32_t *bm = reinterpret_cast<uint32_t *>(sm + cfg.off_gs);  // [Kp / 32] group-start masks
-    float *stage = reinterpret_cast<float *>(sm + cfg.off_stage);  // [8 warps x 32 rows][Gp + 1]
+    float *stage = reinterpret_cast<float *>(sm + cfg.off_stage);  // [2 groups x 128 rows][Gp + 1]
+    float4 *mrg = reinterpret_cast<float4 *>(stage + (size_t)kGroups * kTM * (p.Gp + 1));  // [2 x 128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + cfg.off_bar);
     const int S = cfg.stages;
     uint64_t *full_a = bars;
@@ -93,7 +108,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             bar_init(&full_a[i], 1);
-            bar_init(&empty_a[i], kEpiWarps);
+            bar_init(&empty_a[i], kEpiWarps / 2);  // the warps that read the row norms
         }
         for (int g = 0; g < kGroups; ++g) {
             bar_init(&acc_full[g], 1);
@@ -232,189 +247,224 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // ------------------------------------------------------- epilogue
-        const int grp_id = (warp - 2) / kEpiWarps;
+        // Two warps per TMEM lane quadrant and group: half 0 scans the first
+        // half of the accumulator columns and finishes the rows, half 1 scans
+        // the second half; the pair meets at a 64-thread named barrier (1..8).
+        const int e = warp - 2;
+        const int grp_id = e / kEpiWarps;
+        const int half = (e % kEpiWarps) / 4;
+        const int pid = 1 + grp_id * 4 + ((e % kEpiWarps) & 3);
         const int q = warp & 3;  // TMEM lane quadrant of this warp
         const int r = q * 32 + lane;
         const bool bounds = p.algo == KM_ALGO_FILTERED;
         const float c2max = __fmul_ru(*c2max_s, 1.0f + 1.0f / 1024);
         const float cmax = sqrt_hi(c2max);
         const float ec2 = __fmul_ru(cfg.e_c2, c2max);
-        float *row = stage + (size_t)((warp - 2) * 32 + lane) * (p.Gp + 1);
+        float *row = stage + (size_t)(grp_id * kTM + r) * (p.Gp + 1);  // shared by the pair
+        float4 *mrow = mrg + grp_id * kTM + r;                       // half 1's result for half 0
+        // column chunks of 32: half 0 takes [0, ha), half 1 [ha, nch); half 1's
+        // first store lands in the slot of the group open at its first column's
+        // left neighbour, which half 0 merges with its own last minimum
+        const int nch = Kp >> 5, ha = (nch + 1) >> 1;
+        const int k0 = half ? ha : 0, k1 = half ? nch : ha;
+        const int gsplit = nch > 1 ? group_of(bm, 32 * ha - 1) : 0;
         unsigned long long c_changed = 0, c_recheck = 0, c_dist = 0;
         int i = grp_id;
         for (int tile = blockIdx.x + grp_id * gridDim.x; tile < cfg.num_tiles;
              tile += kGroups * gridDim.x, i += kGroups) {
             const int s = i % S, f = i / S;
             const int u = i / kGroups;
-            // waits are warp-uniform: the TMEM loads below are warp-collective
-            if (!__all_sync(0xffffffffu, bar_wait(&acc_full[grp_id], u & 1, ctrl))) break;
-            if (!__all_sync(0xffffffffu, bar_wait(&full_a[s], f & 1, ctrl))) break;
+            // waits are warp-uniform (the TMEM loads below are warp-collective)
+            // and pair-uniform (the named barriers need both warps)
+            bool ok = __all_sync(0xffffffffu, bar_wait(&acc_full[grp_id], u & 1, ctrl));
+            if (half == 0) ok = ok && __all_sync(0xffffffffu, bar_wait(&full_a[s], f & 1, ctrl));
+            if (!pair_and(ok, pid)) break;
             tc_fence_after();
-            const uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
             const int64_t n = (int64_t)tile * kTM + r;
             const bool valid = n < p.N;
-            // the previous label, read now so that its latency hides behind the scan
-            const int old = valid ? (first ? -1 : p.label[n]) : -1;
-            const float xn = row_norm2<D>(st, st + NA * kAtomBytes, r);
-            // the split copy of A is no longer needed
-            __syncwarp();
-            if (lane == 0) bar_arrive(&empty_a[s]);
-            const float xlo = __fmul_rd(xn, cfg.xn_lo), xup = __fmul_ru(xn, cfg.xn_hi);
-            const float E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
-            const float twoE = __fmul_ru(2.f, E);
+            int old = -1;
+            float xlo = 0.f, xup = 0.f, E = 0.f;
+            if (half == 0) {
+                // the previous label, read now so that its latency hides behind the scan
+                old = valid ? (first ? -1 : p.label[n]) : -1;
+                const uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
+                const float xn = row_norm2<D>(st, st + NA * kAtomBytes, r);
+                // the split copy of A is no longer needed
+                __syncwarp();
+                if (lane == 0) bar_arrive(&empty_a[s]);
+                xlo = __fmul_rd(xn, cfg.xn_lo);
+                xup = __fmul_ru(xn, cfg.xn_hi);
+                E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
+            }
             const uint32_t tb = tmem + (uint32_t)(grp_id * cfg.buf_cols) + ((uint32_t)(q * 32) << 16);
 
-            // pass 1: group minima (staged), winner (lowest index on ties), runner-up;
-            // the next 32 columns are read from TMEM while the current ones are scanned
-            float b1, b2;
-            int i1;
-            {
-                // two runs: chunks [0, ha) and [ha, nch) of 32 columns
-                const int nch = Kp >> 5, ha = (nch + 1) >> 1;
-                RowScan A, B;
-                A.init(row);
-                // run B starts inside the group open at its first column's left
-                // neighbour; its first store lands in that group's slot, which
-                // is merged with run A's last minimum below
-                const int gsplit = nch > 1 ? group_of(bm, 32 * ha - 1) : 0;
-                B.init(row + gsplit);
-                uint32_t ra[32], rb[32];
-                for (int k = 0; k < ha; ++k) {
-                    const bool two = ha + k < nch;  // warp-uniform
-                    tmem_ld32_async(tb + 32 * k, ra);
-                    if (two) tmem_ld32_async(tb + 32 * (ha + k), rb);
-                    tmem_wait32(ra);
-                    if (two) {
-                        tmem_wait32(rb);
-                        scan_pair(A, ra, 32 * k, B, rb, 32 * (ha + k), cn, pen);
-                    } else {
-                        scan_one(A, ra, 32 * k, cn, pen);
-                    }
+            // pass 1: group minima (staged), winner (lowest index on ties), runner-up
+            // over this half's columns; the next 32 columns are read from TMEM
+            // while the current ones are scanned
+            RowScan A;
+            A.init(half ? row + gsplit : row);
+            if (k0 < k1) {  // 16 columns at a time, the next 16 in flight
+                const int c0 = 32 * k0, c1 = 32 * k1;
+                uint32_t ra[16], rb[16];
+                tmem_ld16_async(tb + c0, ra);
+                for (int c = c0; c < c1; c += 32) {  // warp-uniform; c1 - c0 is a multiple of 32
+                    tmem_wait16(ra);
+                    tmem_ld16_async(tb + c + 16, rb);
+                    scan_one<16>(A, ra, c, cn, pen);
+                    tmem_wait16(rb);
+                    if (c + 32 < c1) tmem_ld16_async(tb + c + 32, ra);
+                    scan_one<16>(A, rb, c + 16, cn, pen);
                 }
-                if (nch > 1) {
-                    B.close();
-                    const float gmA = A.gm;
-                    asm volatile("" ::: "memory");
-                    row[gsplit] = fminf(row[gsplit], gmA);
-                } else {
-                    A.close();
-                }
-                float a1, a2, c1, c2;
-                int ai, ci;
-                A.result(a1, ai, a2);
-                B.result(c1, ci, c2);
-                // run A holds the lower indices: it wins ties
-                const bool bw = c1 < a1;
-                b1 = bw ? c1 : a1;
-                i1 = bw ? ci : ai;
-                b2 = fminf(fminf(a2, c2), fmaxf(a1, c1));
-            }
-            const float thr = __fadd_ru(b1, twoE);
-
-            // Rows whose runner-up is inside the error window go to the settle
-            // queue: k_settle decides them exactly afterwards from FP32 (and
-            // FP64) distances to the centroids of the groups whose minimum lies
-            // in the window (every other centroid is strictly farther than the
-            // tensor-core winner i1, which is among them).  The epilogue writes such a
-            // row's bounds as if the tensor-core winner i1 won; k_settle
-            // corrects them when it does not.
-            const bool need = valid && b2 <= thr;
-            {
-                const unsigned nm = __ballot_sync(0xffffffffu, need);
-                if (nm) {
-                    // the groups that can hold a window column: group minimum
-                    // within the window (at most 64 groups; more: all of them)
-                    unsigned long long gmask = ~0ull;
-                    if (G <= 64) {
-                        gmask = 0ull;
-                        for (int g = 0; g < G; ++g) gmask |= (row[g] <= thr) ? (1ull << g) : 0ull;
-                    }
-                    if (need) {
-                        SettleReq rq;
-                        rq.n = (int32_t)n;
-                        rq.old = old;
-                        rq.i1 = i1;
-                        // every column is at least b1: when i1 loses, this bounds both
-                        // i1's group (which now keeps i1) and the winner's group
-                        rq.lb_alt = sqrt_lo(__fsub_rd(__fadd_rd(xlo, b1), E));
-                        rq.gmask = gmask;
-                        rq.lim = 0.f;
-                        p.sreq[n] = rq;
-                    }
-                }
-                // the warp's 32 rows in the request bitmap (every word is written
-                // by every dense pass, so the bitmap needs no clearing)
-                if (lane == 0) p.sbits[(int64_t)tile * (kTM / 32) + q] = nm;
             }
             // accumulators no longer needed
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&acc_empty[grp_id]);
+            if (half) {
+                if (nch > 1) A.close();
+                float c1, c2;
+                int ci;
+                A.result(c1, ci, c2);
+                *mrow = make_float4(c1, c2, __int_as_float(ci), 0.f);
+            }
+            pair_sync(pid);  // half 1's minima and result are in shared memory
+            if (half == 0) {
+                float b1, b2;
+                int i1;
+                {
+                    if (nch > 1) {
+                        const float gmA = A.gm;
+                        row[gsplit] = fminf(row[gsplit], gmA);
+                    } else {
+                        A.close();
+                    }
+                    float a1, a2;
+                    int ai;
+                    A.result(a1, ai, a2);
+                    const float4 m = *mrow;
+                    const float c1 = m.x, c2 = m.y;
+                    const int ci = __float_as_int(m.z);
+                    // half 0 holds the lower indices: it wins ties
+                    const bool bw = c1 < a1;
+                    b1 = bw ? c1 : a1;
+                    i1 = bw ? ci : ai;
+                    b2 = fminf(fminf(a2, c2), fmaxf(a1, c1));
+                }
+                const float twoE = __fmul_ru(2.f, E);
+                const float thr = __fadd_ru(b1, twoE);
 
-            const int best = i1;
-            if (valid) {
-                c_dist += (unsigned long long)K;
-                if (!need) p.label[n] = best;
-                if (bounds) {
-                    // s_c >= xn_lo + t_c - E for every column c
-#pragma unroll 4
-                    for (int g = 0; g < G; ++g) {
-                        const float tg = row[g];
-                        row[g] = tg == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, tg), E));
+                // Rows whose runner-up is inside the error window go to the settle
+                // queue: k_settle decides them exactly afterwards from FP32 (and
+                // FP64) distances to the centroids of the groups whose minimum lies
+                // in the window (every other centroid is strictly farther than the
+                // tensor-core winner i1, which is among them).  The epilogue writes
+                // such a row's bounds as if the tensor-core winner i1 won; k_settle
+                // corrects them when it does not.
+                const bool need = valid && b2 <= thr;
+                {
+                    const unsigned nm = __ballot_sync(0xffffffffu, need);
+                    if (nm) {
+                        // the groups that can hold a window column: group minimum
+                        // within the window (at most 64 groups; more: all of them)
+                        unsigned long long gmask = ~0ull;
+                        if (G <= 64) {
+                            gmask = 0ull;
+                            for (int g = 0; g < G; ++g) gmask |= (row[g] <= thr) ? (1ull << g) : 0ull;
+                        }
+                        if (need) {
+                            SettleReq rq;
+                            rq.n = (int32_t)n;
+                            rq.old = old;
+                            rq.i1 = i1;
+                            // every column is at least b1: when i1 loses, this bounds both
+                            // i1's group (which now keeps i1) and the winner's group
+                            rq.lb_alt = sqrt_lo(__fsub_rd(__fadd_rd(xlo, b1), E));
+                            rq.gmask = gmask;
+                            rq.lim = 0.f;
+                            p.sreq[n] = rq;
+                        }
                     }
-                    // the winner's group must exclude the winner: every other
-                    // column is at least the runner-up b2 (at least b1 when the
-                    // exact winner is not the tensor-core winner)
-                    const float tw = best == i1 ? b2 : b1;
-                    const float lw = tw == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, tw), E));
-                    row[group_of(bm, best)] = lw;
-                    // the bound is monotone in t, so the smallest group bound is
-                    // the bound of the smallest column other than the winner
-                    p.lbg[n] = lw;
-                    p.u[n] = sqrt_hi(__fadd_ru(__fadd_ru(xup, b1), E));
-                    p.stamp[n] = make_stamp(v, v);
+                    // the warp's 32 rows in the request bitmap (every word is written
+                    // by every dense pass, so the bitmap needs no clearing)
+                    if (lane == 0) p.sbits[(int64_t)tile * (kTM / 32) + q] = nm;
+                }
+
+                const int best = i1;
+                if (valid) {
+                    c_dist += (unsigned long long)K;
+                    if (!need) p.label[n] = best;
+                    if (bounds) {
+                        // the winner's group must exclude the winner: every other
+                        // column is at least the runner-up b2 (at least b1 when the
+                        // exact winner is not the tensor-core winner); staged in t
+                        // and converted with the other groups below
+                        const float tw = best == i1 ? b2 : b1;
+                        const float lw = tw == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, tw), E));
+                        row[group_of(bm, best)] = tw;
+                        // the bound is monotone in t, so the smallest group bound is
+                        // the bound of the smallest column other than the winner
+                        p.lbg[n] = lw;
+                        p.u[n] = sqrt_hi(__fadd_ru(__fadd_ru(xup, b1), E));
+                        p.stamp[n] = make_stamp(v, v);
+                    }
+                }
+                *mrow = make_float4(xlo, E, 0.f, 0.f);  // for half 1's share of the conversion
+                {
+                    // label changes: one slot reservation per warp
+                    const bool moved = valid && !need && old != best;
+                    const unsigned mm = __ballot_sync(0xffffffffu, moved);
+                    c_changed += moved ? 1 : 0;
+                    if (mm && !first) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&ctrl->moved_count, __popc(mm));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (moved) {
+                            const int slot = base + __popc(mm & ((1u << lane) - 1u));
+                            p.moved[slot] = (int)n;
+                            p.moved_old[slot] = old;
+                        }
+                    }
                 }
             }
-            {
-                // label changes: one slot reservation per warp
-                const bool moved = valid && !need && old != best;
-                const unsigned mm = __ballot_sync(0xffffffffu, moved);
-                c_changed += moved ? 1 : 0;
-                if (mm && !first) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&ctrl->moved_count, __popc(mm));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (moved) {
-                        const int slot = base + __popc(mm & ((1u << lane) - 1u));
-                        p.moved[slot] = (int)n;
-                        p.moved_old[slot] = old;
-                    }
-                }
-            }
+            pair_sync(pid);  // half 0's winner fixes and (x_lo, E) are in shared memory
             if (bounds) {
-                // the warp's 32 rows (consecutive points) as one contiguous block
-                __syncwarp();
+                // s_c >= xn_lo + t_c - E for every column c: the pair converts the
+                // row's group minima, half 0 the first half of the groups
+                const int gh = (G + 1) >> 1;
+                if (valid) {
+                    const float4 xe = *mrow;
+                    const int g0 = half ? gh : 0, g1 = half ? G : gh;
+#pragma unroll 4
+                    for (int g = g0; g < g1; ++g) {
+                        const float tg = row[g];
+                        row[g] = tg == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xe.x, tg), xe.y));
+                    }
+                }
+                pair_sync(pid);  // the rows' bounds are complete
+                // the quadrant's 32 rows (consecutive points) as one contiguous
+                // block, half 0 the first 16 rows, half 1 the rest
                 const int64_t n0 = (int64_t)tile * kTM + q * 32;
                 const int rows = (int)min((int64_t)32, p.N - n0);
-                if (rows > 0) {
+                const int r0 = half * 16, r1 = min(rows, r0 + 16);
+                if (r1 > r0) {
                     // rows x Gp floats, contiguous in lb: 16-byte stores (Gp is a
                     // multiple of 4, so no vector crosses a row)
                     const int Gp = p.Gp, q4 = Gp >> 2;
-                    const float *st0 = stage + (size_t)((warp - 2) * 32) * (Gp + 1);
+                    const float *st0 = stage + (size_t)(grp_id * kTM + q * 32) * (Gp + 1);
                     float4 *dst = reinterpret_cast<float4 *>(p.lb + n0 * Gp);
-                    for (int e = lane; e < rows * q4; e += 32) {
-                        const int rw = e / q4, g = (e - rw * q4) * 4;
+                    for (int ee = r0 * q4 + lane; ee < r1 * q4; ee += 32) {
+                        const int rw = ee / q4, g = (ee - rw * q4) * 4;
                         const float *src = st0 + rw * (Gp + 1) + g;
                         float4 v4;
                         v4.x = g < G ? src[0] : 0.f;
                         v4.y = g + 1 < G ? src[1] : 0.f;
                         v4.z = g + 2 < G ? src[2] : 0.f;
                         v4.w = g + 3 < G ? src[3] : 0.f;
-                        dst[e] = v4;
+                        dst[ee] = v4;
                     }
                 }
-                __syncwarp();
             }
+            pair_sync(pid);  // the row slots are free for the pair's next tile
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -932,7 +982,7 @@ bool plan(const Params &p, size_t smem_limit, TcCfg &cfg, size_t &smem) {
     const size_t a_stage = 2 * NA * (size_t)kAtomBytes;
     const size_t cn_bytes = (size_t)cfg.Kp * 8;  // norms and group-opening penalties
     const size_t gs_bytes = (((size_t)cfg.Kp / 32) * 4 + 15) & ~size_t(15);  // group-start masks
-    const size_t stage_bytes = (size_t)kGroups * kTM * (p.Gp + 1) * 4;
+    const size_t stage_bytes = (size_t)kGroups * kTM * (p.Gp + 1) * 4 + (size_t)kGroups * kTM * 16;
     const size_t fixed = 1024 + b_bytes + cn_bytes + gs_bytes + stage_bytes + 64 * 8 + 64;
     if (fixed + 2 * a_stage > smem_limit) return false;
     cfg.stages = (int)std::min<size_t>(6, (smem_limit - fixed) / a_stage);
