@@ -264,8 +264,7 @@ KERNEL_SOURCES = {
     "filter": ["paper_1905_09345_gb300/csrc/kp_filter.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "survivor": ["paper_1905_09345_gb300/csrc/kp_survivor_tp.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "update": ["paper_1905_09345_gb300/csrc/kp_update.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
-    "settle": ["paper_1905_09345_gb300/csrc/kp_dense_tc.cu", "paper_1905_09345_gb300/csrc/kp_tc.cuh",
-               "paper_1905_09345_gb300/csrc/kp_common.cuh"],
+    "settle": ["paper_1905_09345_gb300/csrc/kp_settle.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
     "stats": ["paper_1905_09345_gb300/csrc/kp_stats.cu", "paper_1905_09345_gb300/csrc/kp_common.cuh"],
 }
 

@@ -55,6 +55,7 @@ struct Ctrl {
     int32_t surv_next;     // next queue entry to hand out in the survivor kernel
     int32_t stats_full;    // the cluster sums of this iteration are recomputed in full
     uint32_t stats_ticket; // last-block-done counter of k_stats_hist
+    int32_t settle_next;   // next settle request to hand out
 };
 
 // Device-side error codes in Ctrl::err (0 = none).

@@ -23,7 +23,9 @@
 //     the best and the value that includes it, in case the best moves on;
 //   * a point whose FP32 best and runner-up cannot be separated by the FP32
 //     error bound is settled over all K centroids, in FP64 where needed, and
-//     its bounds are rebuilt from that full scan;
+//     its bounds are rebuilt from that full scan -- by the whole warp, after
+//     the batch's points are done, so that one lane does not hold up the
+//     other 31 (and the SM) for the length of a K-centroid scan;
 //   * label changes go to the moved-point list; the cluster sums are updated
 //     by the moves kernel afterwards.
 #include "kp_common.cuh"
@@ -89,16 +91,46 @@ __device__ __forceinline__ void load_x(const Params &p, int64_t n, ulonglong2 (&
     }
 }
 
-// FP64 squared distance, coordinates ascending, no fused multiply-add (the
-// summation order of the FP64 definition)
+// Distances with the point read from memory instead of registers (the warp's
+// settle below keeps no copy of the row, which keeps the survivor kernel free
+// of spills): coordinates are loaded and packed exactly as load_x does, four
+// at a time, so sqdist_mem rounds every step as sqdist_xr does on load_x's
+// result.  dist2_f64_mem is the FP64 squared distance, coordinates ascending,
+// no fused multiply-add (the summation order of the FP64 definition).
 template <int DP>
-__device__ __forceinline__ double dist2_f64_xr(const ulonglong2 (&xr)[DP / 4], const float *__restrict__ c, int D) {
-    double s = 0.0;
-#pragma unroll
+__device__ __forceinline__ ulonglong2 x_quad(const Params &p, const float *xg, int q) {
+    const int D = p.D;
+    if (p.x_vec4) return 4 * q < D ? __ldg(reinterpret_cast<const ulonglong2 *>(xg) + q) : make_ulonglong2(0ull, 0ull);
+    const float x0 = 4 * q + 0 < D ? __ldg(xg + 4 * q + 0) : 0.f;
+    const float x1 = 4 * q + 1 < D ? __ldg(xg + 4 * q + 1) : 0.f;
+    const float x2 = 4 * q + 2 < D ? __ldg(xg + 4 * q + 2) : 0.f;
+    const float x3 = 4 * q + 3 < D ? __ldg(xg + 4 * q + 3) : 0.f;
+    return make_ulonglong2(pack2(x0, x1), pack2(x2, x3));
+}
+template <int DP>
+__device__ __forceinline__ float sqdist_mem(const Params &p, const float *xg, const float *__restrict__ c) {
+    unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll 4
     for (int q = 0; q < DP / 4; ++q) {
+        const ulonglong2 x2 = x_quad<DP>(p, xg, q);
+        const ulonglong2 c2 = *reinterpret_cast<const ulonglong2 *>(c + 4 * q);
+        unsigned long long d0, d1;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(x2.x), "l"(c2.x));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(x2.y), "l"(c2.y));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a0) : "l"(d0));
+        asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a1) : "l"(d1));
+    }
+    return hsum2(a0) + hsum2(a1);
+}
+template <int DP>
+__device__ __forceinline__ double dist2_f64_mem(const Params &p, const float *xg, const float *__restrict__ c) {
+    const int D = p.D;
+    double s = 0.0;
+    for (int q = 0; q < DP / 4; ++q) {
+        const ulonglong2 x2 = x_quad<DP>(p, xg, q);
         float xv[4];
-        unpack2(xr[q].x, xv[0], xv[1]);
-        unpack2(xr[q].y, xv[2], xv[3]);
+        unpack2(x2.x, xv[0], xv[1]);
+        unpack2(x2.y, xv[2], xv[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (4 * q + j < D) {
@@ -110,45 +142,61 @@ __device__ __forceinline__ double dist2_f64_xr(const ulonglong2 (&xr)[DP / 4], c
     return s;
 }
 
-// Rare path: the FP32 results do not separate the best (FP32 value s1, index
-// i1) from the runner-up.  Every centroid whose FP32 distance the error bound
-// cannot separate from s1 is settled in FP64 (lowest index on equal FP64
-// distances).  When the FP64 winner is not i1, every group bound is rebuilt
-// from a full FP32 scan (the bounds written by the filtered scan assumed i1).
-// Returns the winner; *s_win is its FP32 squared distance.
+// Rare path, taken by the whole warp for one point: the FP32 results do not
+// separate the best (FP32 value s1, index i1) from the runner-up.  The lanes
+// take the centroids lane, lane + 32, ...; every centroid whose FP32 distance
+// the error bound cannot separate from s1 is settled in FP64, and the warp
+// keeps the smallest FP64 distance (lowest index on equal distances).  When
+// that winner is not i1, every group bound is rebuilt from FP32 distances,
+// one lane per group (the bounds written by the filtered scan assumed i1),
+// and *lbg_out receives their minimum.  All lanes return the winner; *s_win
+// is its FP32 squared distance.  (One lane alone took about 125 us for this
+// at K = 256, D = 64, against about 28 us for a whole batch of 32 points.)
 template <int DP>
-__device__ __noinline__ int settle_full(const Params &p, const float *Cs, const int32_t *gs, int64_t n, float s1,
+__device__ __forceinline__ int settle_warp(const Params &p, const float *Cs, const int32_t *gs, int64_t n, float s1,
                                         int i1, float *s_win, float *lbg_out) {
     const int K = p.K, G = p.G, D = p.D;
-    ulonglong2 xr[DP / 4];
-    load_x<DP>(p, n, xr);
+    const int lane = threadIdx.x & 31;
+    const float *xg = p.X + n * D;
     double bd = INFINITY;
-    int bi = i1;
-    for (int c = 0; c < K; ++c) {
-        const float s = sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp);
+    int bi = 0x7fffffff;
+    for (int c = lane; c < K; c += 32) {  // ascending: the first of equal distances stays
+        const float s = sqdist_mem<DP>(p, xg, Cs + (size_t)c * p.Dp);
         if (!unresolved(s1, s, p)) continue;
-        const double d = dist2_f64_xr<DP>(xr, Cs + (size_t)c * p.Dp, D);
-        if (d < bd || (d == bd && c < bi)) {
+        const double d = dist2_f64_mem<DP>(p, xg, Cs + (size_t)c * p.Dp);
+        if (d < bd) {
             bd = d;
             bi = c;
         }
     }
-    if (bi == i1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (od < bd || (od == bd && oi < bi)) {
+            bd = od;
+            bi = oi;
+        }
+    }
+    // i1 is always among the unresolved centroids (its own distance is s1)
+    if (bi == 0x7fffffff || bi == i1) {
         *s_win = s1;
-        return bi;
+        return i1;
     }
     float lmin = INFINITY;
     float *lbrow = p.lb + n * p.Gp;
-    for (int g = 0; g < G; ++g) {
+    for (int g = lane; g < G; g += 32) {
         float m = INFINITY;
         for (int c = gs[g]; c < gs[g + 1]; ++c) {
             if (c == bi) continue;
-            m = fminf(m, dist_dn(sqdist_xr<DP>(xr, Cs + (size_t)c * p.Dp), p));
+            m = fminf(m, dist_dn(sqdist_mem<DP>(p, xg, Cs + (size_t)c * p.Dp), p));
         }
         lbrow[g] = m;
         lmin = fminf(lmin, m);
     }
-    *s_win = sqdist_xr<DP>(xr, Cs + (size_t)bi * p.Dp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    *s_win = sqdist_mem<DP>(p, xg, Cs + (size_t)bi * p.Dp);
     *lbg_out = lmin;
     return bi;
 }
@@ -212,6 +260,10 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
         bool moved = false;
         int64_t n = 0;
         int a = 0;
+        // a point deferred to the warp's settle: its FP32 best, index and global bound
+        bool rc = false;
+        float rc_s = 0.f, rc_lbg = 0.f;
+        int rc_best = 0;
         if (active) {
             n = p.queue[it];
             a = p.label[n];
@@ -360,16 +412,45 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
                 float lbg_new = bg >= 0 ? fminf(lmin, bg_val) : lmin;
 
                 if (s_sec != INFINITY && unresolved(s_best, s_sec, p)) {
-                    best = settle_full<DP>(p, Cs, gs, n, s_best, best, &s_best, &lbg_new);
-                    c_dist += (unsigned long long)K;
-                    c_recheck += 1;
+                    rc = true;  // settled by the warp below
+                    rc_s = s_best;
+                    rc_best = best;
+                    rc_lbg = lbg_new;
+                } else {
+                    p.lbg[n] = lbg_new;
+                    p.u[n] = dist_up(s_best, p);
+                    p.label[n] = best;
+                    p.stamp[n] = make_stamp(v, v);
+                    moved = best != a;
                 }
-                p.lbg[n] = lbg_new;
-                p.u[n] = dist_up(s_best, p);
-                p.label[n] = best;
-                p.stamp[n] = make_stamp(v, v);
-                moved = best != a;
             }
+        }
+        // the batch's unresolved points, one at a time by the whole warp (its
+        // lanes' bound-row stores above are ordered before the rebuild's)
+        __syncwarp();
+        unsigned rm = __ballot_sync(0xffffffffu, rc);
+        while (rm) {
+            const int src = __ffs(rm) - 1;
+            rm &= rm - 1;
+            const int64_t nr = __shfl_sync(0xffffffffu, n, src);
+            const float s1 = __shfl_sync(0xffffffffu, rc_s, src);
+            const int i1 = __shfl_sync(0xffffffffu, rc_best, src);
+            float sw = s1, lg = __shfl_sync(0xffffffffu, rc_lbg, src);
+            const int w = settle_warp<DP>(p, Cs, gs, nr, s1, i1, &sw, &lg);
+            if (lane == src) {
+                rc_best = w;
+                rc_s = sw;
+                rc_lbg = lg;
+            }
+        }
+        if (rc) {
+            p.lbg[n] = rc_lbg;
+            p.u[n] = dist_up(rc_s, p);
+            p.label[n] = rc_best;
+            p.stamp[n] = make_stamp(v, v);
+            moved = rc_best != a;
+            c_dist += (unsigned long long)K;
+            c_recheck += 1;
         }
         // moved points: one atomic per warp for the list slots
         const unsigned mm = __ballot_sync(0xffffffffu, moved);

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         ctrl->moved_count = 0;
         ctrl->settle_count = 0;
         ctrl->surv_next = 0;
+        ctrl->settle_next = 0;
         ctrl->path = KM_PATH_FILTERED;
         ctrl->dense_mode = 0;
         __threadfence();
