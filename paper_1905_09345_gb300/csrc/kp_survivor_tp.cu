@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
         bool rc = false;
         float rc_s = 0.f, rc_lbg = 0.f;
         int rc_best = 0;
+        const unsigned long long c_dist0 = c_dist;  // this lane's count before its point
         if (active) {
             n = p.queue[it];
             a = p.label[n];
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
             p.label[n] = rc_best;
             p.stamp[n] = make_stamp(v, v);
             moved = rc_best != a;
-            c_dist += (unsigned long long)K;
+            c_dist = c_dist0 + (unsigned long long)K;  // evaluated against all K: K, not scan + K
             c_recheck += 1;
         }
         // moved points: one atomic per warp for the list slots

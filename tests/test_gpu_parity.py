@@ -251,6 +251,37 @@ def test_exact_ties_go_to_lowest_index(kp):
     assert st[0]["n_recheck"] > 0  # the ties went through the FP64 settle
 
 
+@pytest.mark.parametrize("D", [4, 64])
+@pytest.mark.parametrize("dense_switch", [0.0, 1.0])
+def test_persistent_exact_ties(kp, D, dense_switch):
+    """Blobs of integer offsets (symmetric about integer centres) and every
+    centre given twice, the copies in the other group: each point is exactly
+    as far from both copies in every iteration (the first copy's mean stays
+    its centre, the second copy stays empty), so every iteration settles
+    near-ties -- on the survivor path with the filters alone (dense_switch
+    1), in the dense passes otherwise, where D = 64 runs on the tensor cores
+    -- and the lowest index must win each time.  Many ties per warp exercise
+    the warp-wide settles one request after another."""
+    rng = np.random.default_rng(5)
+    k = 8
+    centres = rng.choice(np.arange(-40, 41, 10), size=(k, 2), replace=True).astype(np.float32)
+    centres[:, 0] = np.arange(k) * 10 - 35  # distinct centres
+    o = np.arange(-2, 3, dtype=np.float32)
+    off = np.stack(np.meshgrid(o, o), -1).reshape(-1, 2)
+    X = np.zeros((k * off.shape[0], D), np.float32)
+    X[:, :2] = (centres[:, None, :] + off[None]).reshape(-1, 2)
+    X = X[rng.permutation(X.shape[0])]
+    C0 = np.zeros((2 * k, D), np.float32)
+    C0[:k, :2] = centres
+    C0[k:, :2] = centres
+    st = lockstep(kp, X, C0, 2, 4, dense_switch=dense_switch)
+    assert all(s["n_recheck"] > 0 for s in st), [s["n_recheck"] for s in st]
+    if dense_switch >= 1.0:
+        assert all(s["path"] == kp.KM_PATH_FILTERED for s in st[1:]), [s["path"] for s in st]
+    if D == 64:
+        assert st[0]["path"] == kp.KM_PATH_DENSE_TC
+
+
 def test_k_equals_n(kp):
     rng = np.random.default_rng(3)
     X = rng.standard_normal((64, 5)).astype(np.float32)
