@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -107,7 +108,10 @@ class ClockSampler:
     def __init__(self, gpu_id: str | None):
         self.gpu_id = gpu_id
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples in a scratch file (KPYNQ_CLOCKS_DIR, else the system's
+        # temporary directory); the JSON line carries their summary
+        d = os.environ.get("KPYNQ_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"kpynq_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
