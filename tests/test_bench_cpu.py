@@ -17,11 +17,12 @@ def _it(i, path, surv=0, scan=0, nd=0):
 
 def test_dense_bytes_per_launch():
     w = _w()
-    (b, units), = bench.algorithmic("dense_assign", w, [_it(0, 2)], 1)
+    out = dict(bench.algorithmic("dense_assign", w, [_it(0, 2)], 1))
     # X (4 bytes per coordinate), label/u/lbg/stamp, and the lb row with G rounded to 4
-    assert b == "hbm" and units == w.N * (4 * 64 + 16 + 4 * 28)
+    assert out["hbm"] == w.N * (4 * 64 + 16 + 4 * 28)
+    assert out["tensor"] == 6.0 * w.N * w.K * w.D and "alu" not in out  # BF16x3 on the tensor cores
     out = dict(bench.algorithmic("dense_assign", w, [_it(0, 1)], 1))
-    assert out["alu"] == 3.0 * w.N * w.K * w.D  # FP32 engine: every distance
+    assert out["alu"] == 3.0 * w.N * w.K * w.D and "tensor" not in out  # FP32 engine: every distance
 
 
 def test_survivor_units_count_filtered_iterations_only():
