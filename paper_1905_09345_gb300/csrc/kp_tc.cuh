@@ -174,25 +174,6 @@ struct RowScan {
     }
 };
 
-// two runs of 32 columns each (chunks ca of run A and cb of run B), column by
-// column; cn / pen read four columns at a time
-__device__ __forceinline__ void scan_pair(RowScan &A, const uint32_t (&ra)[32], int ca, RowScan &B,
-                                          const uint32_t (&rb)[32], int cb, const float *cn, const float *pen) {
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-        const float4 na = *reinterpret_cast<const float4 *>(cn + ca + j);
-        const float4 pa = *reinterpret_cast<const float4 *>(pen + ca + j);
-        const float4 nb = *reinterpret_cast<const float4 *>(cn + cb + j);
-        const float4 pb = *reinterpret_cast<const float4 *>(pen + cb + j);
-        const float nav[4] = {na.x, na.y, na.z, na.w}, pav[4] = {pa.x, pa.y, pa.z, pa.w};
-        const float nbv[4] = {nb.x, nb.y, nb.z, nb.w}, pbv[4] = {pb.x, pb.y, pb.z, pb.w};
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            A.col(__uint_as_float(ra[j + jj]), nav[jj], pav[jj], ca + j + jj, jj & 1);
-            B.col(__uint_as_float(rb[j + jj]), nbv[jj], pbv[jj], cb + j + jj, jj & 1);
-        }
-    }
-}
 template <int W>
 __device__ __forceinline__ void scan_one(RowScan &A, const uint32_t (&ra)[W], int ca, const float *cn,
                                          const float *pen) {
