@@ -16,7 +16,7 @@ Two independent C implementations, each written from its definition:
   FP64, with per-iteration skip counters.
 
 * ``mlp.py`` (O3): the learned group proposal's MLP (GELU layers, softmax
-  cross-entropy, Adam) in numpy FP64 -- a layered form of this build, not in
+  cross-entropy, Adam) in numpy FP64 -- a layered form of the library, not in
   the paper; the filtered method's labels do not depend on it.
 
 Pins (``tests/test_oracle_*.py``, ``-m "not gpu"``): closed forms (K = 1 mean,

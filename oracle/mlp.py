@@ -3,7 +3,7 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs may
 import this module; the product library never does.
 
-The paper names no learned component; the proposal is this build's layered
+The paper names no learned component; the proposal is the library's layered
 form on top of the filtered method (its labels are the filtered method's,
 exactly).  What it computes, written from the definitions:
 
