@@ -157,6 +157,32 @@ def contiguous_groups(K: int, G: int) -> np.ndarray:
     return ((np.arange(K, dtype=np.int64) * G) // K).astype(np.int32)
 
 
+def clustered_groups(C, G: int, iters: int = 5) -> np.ndarray:
+    """The clustered grouping (the Yinyang-style reading of how groups form;
+    the paper does not say): Lloyd's algorithm over the K centroids
+    themselves, in FP64, seeded with their first G rows, for ``iters``
+    iterations; centroid k joins the group whose centre is nearest (lowest
+    index on ties) after the last update.  An empty group keeps its centre.
+    Labels of the filtered method do not depend on the grouping; only how
+    much the filters skip does."""
+    C = _as64(C)
+    K = C.shape[0]
+    if not 1 <= G <= K:
+        raise ValueError("need 1 <= G <= K")
+    centres = C[:G].copy()
+    grp = np.zeros(K, np.int32)
+    for it in range(iters + 1):
+        d = ((C[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)
+        grp = np.argmin(d, axis=1).astype(np.int32)  # first minimum: lowest index
+        if it == iters:
+            break
+        for g in range(G):
+            m = grp == g
+            if m.any():
+                centres[g] = C[m].mean(axis=0)
+    return grp
+
+
 # ----------------------------------------------------------------------------
 # O1: brute-force Lloyd
 # ----------------------------------------------------------------------------
