@@ -19,12 +19,17 @@ Two independent C implementations, each written from its definition:
   cross-entropy, Adam) in numpy FP64 -- a layered form of the library, not in
   the paper; the filtered method's labels do not depend on it.
 
+Groupings for O2: ``contiguous_groups`` (centroid j -> group floor(jG/K)) and
+``clustered_groups`` (Lloyd over the centroids, seeded by their first G rows);
+the paper does not say how groups form, and labels do not depend on it.
+
 Pins (``tests/test_oracle_*.py``, ``-m "not gpu"``): closed forms (K = 1 mean,
 K = N zero objective), a hand-derived worked example (``tests/golden``),
 scipy ``cdist`` and scikit-learn's Lloyd as independent library routines,
 Lloyd invariants (monotone objective, fixed point), exact tie cases, O2 == O1
-label-for-label every iteration, O2 bound validity, and planted mistakes that
-the pins must catch.
+label-for-label every iteration (under contiguous, clustered, random and
+partly empty groupings), O2 bound validity, the clustered grouping's fixed
+point and degenerate cases, and planted mistakes that the pins must catch.
 """
 from __future__ import annotations
 
