@@ -150,7 +150,9 @@ typedef struct {
     int64_t n_changed;     /* labels that changed (N at t = 0) */
     int64_t n_survivors;   /* points not kept by the global filter */
     int64_t n_scanned;     /* points still unresolved after tightening u */
-    int64_t n_dist;        /* point-centroid distances evaluated */
+    int64_t n_dist;        /* point-centroid distances evaluated: K per point in a dense
+                              pass, and at most K per point otherwise (a point the FP32
+                              results could not settle counts K, not its scan plus K) */
     int64_t n_recheck;     /* points whose label was settled in FP64 */
     double objective;      /* J_t = J(a_t, C^t) */
     double max_drift;      /* max_k ||c_k^{t+1} - c_k^t|| (rounded up) */
