@@ -262,8 +262,9 @@ KM_API int kmeans_get_iteration(const kmeans_ctx *ctx, int32_t *t);
  * that loads the library holds until the process exits.  Hence the limits
  * K <= KM_NOALLOC_MAX_K and D <= KM_NOALLOC_MAX_D (larger sizes: KM_EINVAL).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and clears what
+ * (cudaGetSymbolAddress) with that device current, and so does the first
+ * call after the device's context was made anew (after cudaDeviceReset);
+ * make that first call before any stream capture.  Every call shares the one array and clears what
  * it accumulates into, so calls that overlap on the GPU (on different
  * streams, or from threads without ordering) race and give wrong results.
  * No cudaMalloc, cudaFree or allocating library routine is called.  Errors:
@@ -339,12 +340,80 @@ KM_API void kmeans_batch_destroy(kmeans_batch *b);
  * kmeans_batch_init in this thread). */
 KM_API const char *kmeans_batch_last_error(const kmeans_batch *b);
 
+/* ------------------------------------------------------------------------
+ * The proposal network on the tensor cores: training and inference.
+ *
+ * A layered form on top of the filtered method (the paper has no learned
+ * component): a multilayer perceptron  D -> hidden -> hidden -> classes  with
+ * GELU activations (the exact erf form), trained with softmax cross-entropy
+ * (mean over the batch) and Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected
+ * moments) on FP32 master weights.  Every matrix product runs on tcgen05 with
+ * bfloat16 operands (weights, inputs, activations and backpropagated
+ * gradients rounded to bfloat16) and FP32 accumulation; the bias, GELU,
+ * softmax, loss, gradient and update arithmetic is FP32.  Parameters are one
+ * FP32 vector in the order W1 (hidden x D), b1, W2 (hidden x hidden), b2,
+ * W3 (classes x hidden), b3 -- row-major, output index first (z = W a + b).
+ * Limits: D <= 256, hidden <= 256, classes <= 512.  All work is ordered on
+ * the stream given at creation; every call below returns after it finished.
+ * Errors: KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT (a bounded wait in a
+ * tensor-core product gave up); message in kmeans_mlp_last_error.
+ * ------------------------------------------------------------------------ */
+typedef struct kmeans_mlp kmeans_mlp;
+
+/* Create a network on the current device with Xavier-uniform weights
+ * (U(-a, a), a = sqrt(6 / (fan_in + fan_out)), from a counter-based
+ * generator seeded with `seed`) and zero biases.  On failure *out is NULL
+ * and kmeans_mlp_last_error(NULL) has the message. */
+KM_API int kmeans_mlp_create(kmeans_mlp **out, int32_t D, int32_t hidden, int32_t classes, uint64_t seed,
+                             void *stream);
+
+/* Replace the FP32 master weights (six arrays, host or device) and restart
+ * Adam (zero moments, step 0). */
+KM_API int kmeans_mlp_set_params(kmeans_mlp *m, const float *W1, const float *b1, const float *W2, const float *b2,
+                                 const float *W3, const float *b3);
+
+/* Copy the FP32 master weights out (each pointer nullable; host or device). */
+KM_API int kmeans_mlp_get_params(kmeans_mlp *m, float *W1, float *b1, float *W2, float *b2, float *W3, float *b3);
+
+/* One forward and backward pass on a given batch, without an update: X is
+ * B x D FP32, y B class indices (device memory), B a multiple of 128.  Writes
+ * the gradient of the mean cross-entropy with respect to every parameter to
+ * grad (device, the parameter vector's layout) and the mean loss to *loss
+ * (nullable). */
+KM_API int kmeans_mlp_gradient(kmeans_mlp *m, const float *X, const int32_t *y, int32_t B, double *loss,
+                               float *grad);
+
+/* `steps` Adam steps (learning rate lr) on batches of `batch` rows (a
+ * multiple of 128) drawn with replacement from the N training rows (X N x D
+ * FP32, labels N int32; device memory) by a counter-based generator seeded
+ * with `seed`; seed ~0 instead takes rows 0 .. batch-1 in every step (plain
+ * full-batch steps, N >= batch).  With K > 0 the labels are centroid indices
+ * in [0, K) and the class of a row is its centroid's contiguous group,
+ * floor(label * classes / K); with K = 0 they are the classes themselves.
+ * One step is recorded once as a CUDA graph and replayed.  *mean_loss and
+ * *accuracy (nullable) receive the mean cross-entropy and the fraction of
+ * rows whose largest logit was their class, over the rows of all steps. */
+KM_API int kmeans_mlp_train(kmeans_mlp *m, const float *X, int64_t N, const int32_t *labels, int32_t K,
+                            int64_t steps, int32_t batch, float lr, uint64_t seed, double *mean_loss,
+                            double *accuracy);
+
+/* pred[n] = the class with the largest logit (the first on ties) for N rows
+ * of X (N x D FP32; X and pred device memory), in chunks of up to 2^17 rows. */
+KM_API int kmeans_mlp_predict_net(kmeans_mlp *m, const float *X, int64_t N, int32_t *pred);
+
+KM_API void kmeans_mlp_destroy(kmeans_mlp *m);
+
+/* Message of the last failure on m (m NULL: of the calling thread's last
+ * failed kmeans_mlp_create). */
+KM_API const char *kmeans_mlp_last_error(const kmeans_mlp *m);
+
 /* Learned group proposal (a layered form on top of the filtered method; the
  * paper has no learned component).  An MLP  D -> hidden -> hidden -> G  with
  * GELU activations (the exact erf form) predicts each point's group as the
- * largest of its G logits.  Weights row-major, output index first:
- * W1 hidden x D, b1 hidden, W2 hidden x hidden, b2 hidden, W3 G x hidden,
- * b3 G (FP32, host or device; copied).  With a proposal set, iteration 0 of
+ * largest of its G logits, on the tensor cores (the network above).  Weights
+ * row-major, output index first: W1 hidden x D, b1 hidden, W2 hidden x
+ * hidden, b2 hidden, W3 G x hidden, b3 G (FP32, host or device; copied;
+ * hidden <= 256, D <= 256, G <= 512).  With a proposal set, iteration 0 of
  * the filtered method (KM_ALGO_FILTERED only) replaces its dense pass by:
  * the prediction; exact FP32 distances to the predicted group's centroids,
  * giving a label candidate c and u >= d(x, c); group bounds by the triangle
@@ -352,18 +421,19 @@ KM_API const char *kmeans_batch_last_error(const kmeans_batch *b);
  * centroid distances; then the ordinary filtered assignment (global, group
  * and point filters, distance calculator; Sec. I), so labels are exactly
  * those without a proposal -- a wrong prediction only costs work.  All six
- * pointers NULL: remove the proposal.  Allocates the weights, N int32
- * predictions, two chunk buffers of min(N, 2^20) x hidden floats and the
- * K x G table.  Errors: KM_EINVAL (Lloyd context, hidden outside [1, 4096],
- * some pointers NULL), KM_ENOMEM, KM_ECUDA. */
+ * pointers NULL: remove the proposal.  Allocates the network, N int32
+ * predictions, its chunk buffers and the K x G table.  Errors: KM_EINVAL
+ * (Lloyd context, hidden outside [1, 256], D > 256 or G > 512, some pointers
+ * NULL), KM_ENOMEM, KM_ECUDA. */
 KM_API int kmeans_set_proposal(kmeans_ctx *c, const float *W1, const float *b1, const float *W2, const float *b2,
                                const float *W3, const float *b3, int32_t hidden);
 
 /* The proposal MLP alone: pred[n] = argmax_g logits(X[n]) (first maximum)
- * for N points of dimension D, G classes; weights as above.  X, the weights
- * and pred are device memory of the current device; ordered on `stream`
- * (NULL = legacy default), which also holds two temporary chunk buffers
- * (stream-ordered allocation).  Errors: KM_EINVAL, KM_ECUDA; message in
+ * for N points of dimension D, G classes; weights as above (FP32, rounded to
+ * bfloat16 for the tensor-core products).  X and pred are device memory of
+ * the current device; the work runs on `stream` (NULL = legacy default) with
+ * a temporary network, and the call returns after it finished.  Errors:
+ * KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT; message in
  * kmeans_last_error(NULL). */
 KM_API int kmeans_mlp_predict(const float *X, int64_t N, int32_t D, const float *W1, const float *b1,
                               const float *W2, const float *b2, const float *W3, const float *b3, int32_t hidden,

@@ -44,13 +44,12 @@ struct kmeans_ctx {
     float *X_own = nullptr;
     int tcap = 0;
     bool use_tc = false;   // dense passes on the tensor cores
-    // learned proposal (kmeans_set_proposal): weights W1|b1|W2|b2|W3|b3, the
-    // predictions, two chunk buffers and the centroid-distance table
+    // learned proposal (kmeans_set_proposal): the network (tensor-core
+    // inference), the predictions and the centroid-distance table
     bool proposal = false;
-    int mlp_h = 0;
-    float *mlp = nullptr, *mlp_a1 = nullptr, *mlp_a2 = nullptr, *cc_table = nullptr;
+    kmeans_mlp *net = nullptr;
+    float *cc_table = nullptr;
     int32_t *pred = nullptr;
-    int64_t mlp_chunk = 0;
     bool have_final = false;  // a fit finished: its final-assignment record is kept
     int t_host = 0;        // iterations run (mirrors ctrl->t after each call)
     int v_host = 0;        // table version (mirrors ctrl->v)
@@ -332,13 +331,8 @@ cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int f
 // Iteration 0 seeded by the learned proposal: predictions, the centroid
 // table and the seeded bounds (the filtered assignment follows).
 cudaError_t enqueue_proposal(kmeans_ctx *c, const Params &p, cudaStream_t s, int respect_done) {
-    const int H = c->mlp_h, D = p.D, G = p.G;
-    const float *W1 = c->mlp, *b1 = W1 + (size_t)H * D, *W2 = b1 + H, *b2 = W2 + (size_t)H * H, *W3 = b2 + H,
-                *b3 = W3 + (size_t)G * H;
     return timed(c, s, KM_KERNEL_PROPOSAL, [&] {
-        cudaError_t e = launch_mlp_predict(p.X, p.N, D, W1, b1, W2, b2, W3, b3, H, G, c->pred, c->mlp_a1, c->mlp_a2,
-                                           c->mlp_chunk, s);
-        if (e != cudaSuccess) return e;
+        if (mlp_predict_enqueue(c->net, p.X, p.N, c->pred, s) != KM_OK) return cudaErrorLaunchFailure;
         return launch_proposal_seed(p, c->pred, c->cc_table, s, respect_done, c->num_sms);
     });
 }
@@ -612,6 +606,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     INIT_CUDA(dalloc(c, &p.C, (size_t)K * p.Dp));
     INIT_CUDA(dalloc(c, &p.S, (size_t)K * D));
     INIT_CUDA(dalloc(c, &p.Q, (size_t)K));
+    INIT_CUDA(dalloc(c, &p.R, (size_t)K * p.Dp));
     INIT_CUDA(dalloc(c, &p.cnt, (size_t)K));
     INIT_CUDA(dalloc(c, &p.delta, (size_t)K));
     INIT_CUDA(dalloc(c, &p.Jk, (size_t)K));
@@ -633,6 +628,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     INIT_CUDA(cudaMemsetAsync(p.C, 0, (size_t)K * p.Dp * 4, s));
     INIT_CUDA(cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)D * 4, (size_t)D * 4, K,
                                 cudaMemcpyDefault, s));
+    INIT_CUDA(cudaMemcpyAsync(p.R, p.C, (size_t)K * p.Dp * 4, cudaMemcpyDeviceToDevice, s));
     INIT_CUDA(cudaMemsetAsync(p.S, 0, (size_t)K * D * 8, s));
     INIT_CUDA(cudaMemsetAsync(p.Q, 0, (size_t)K * 8, s));
     INIT_CUDA(cudaMemsetAsync(p.cnt, 0, (size_t)K * 8, s));
@@ -853,6 +849,7 @@ KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
     c->kernels_base += (long long)c->ctrl_host->kernels;
     KP_CUDA(c, cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)p.D * 4, (size_t)p.D * 4, p.K,
                                  cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaMemcpyAsync(p.R, p.C, (size_t)p.K * p.Dp * 4, cudaMemcpyDeviceToDevice, s));
     KP_CUDA(c, cudaMemsetAsync(p.S, 0, (size_t)p.K * p.D * 8, s));
     KP_CUDA(c, cudaMemsetAsync(p.Q, 0, (size_t)p.K * 8, s));
     KP_CUDA(c, cudaMemsetAsync(p.cnt, 0, (size_t)p.K * 8, s));
@@ -894,6 +891,7 @@ KM_API void kmeans_destroy(kmeans_ctx *c) {
     if (c->stream || c->cap_stream) cudaStreamSynchronize(c->stream);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->net) kmeans_mlp_destroy(c->net);
     for (auto &q : c->pending) {
         c->ev_pool.push_back(q.a);
         c->ev_pool.push_back(q.b);
@@ -915,33 +913,27 @@ KM_API int kmeans_set_proposal(kmeans_ctx *c, const float *W1, const float *b1, 
         return set_err(c, KM_EINVAL, "the proposal needs all six weight arrays (or none)");
     if (!none && c->p.algo != KM_ALGO_FILTERED)
         return set_err(c, KM_EINVAL, "the proposal seeds the filtered method's bounds (KM_ALGO_FILTERED only)");
-    if (!none && (hidden < 1 || hidden > 4096)) return set_err(c, KM_EINVAL, "hidden=%d outside [1, 4096]", hidden);
+    if (!none && (hidden < 1 || hidden > 256)) return set_err(c, KM_EINVAL, "hidden=%d outside [1, 256]", hidden);
+    if (!none && (c->p.D > 256 || c->p.G > 512))
+        return set_err(c, KM_EINVAL, "the proposal network takes D <= 256 and G <= 512");
     DeviceGuard dg(c->dev);
     if ((rc = sync_and_check(c))) return rc;
     Params &p = c->p;
-    cudaStream_t s = c->stream;
-    if (none) {
-        c->proposal = false;
-    } else {
-        const int D = p.D, G = p.G, H = hidden;
-        const size_t nw = (size_t)H * D + H + (size_t)H * H + H + (size_t)G * H + G;
-        if (H != c->mlp_h) {  // buffers sized for this hidden width (earlier ones stay until destroy)
-            c->mlp_chunk = std::min<int64_t>(p.N, (int64_t)1 << 20);
-            KP_CUDA(c, dalloc(c, &c->mlp, nw));
-            KP_CUDA(c, dalloc(c, &c->mlp_a1, (size_t)c->mlp_chunk * H));
-            KP_CUDA(c, dalloc(c, &c->mlp_a2, (size_t)c->mlp_chunk * H));
-            if (!c->pred) KP_CUDA(c, dalloc(c, &c->pred, (size_t)p.N));
-            if (!c->cc_table) KP_CUDA(c, dalloc(c, &c->cc_table, (size_t)p.K * G));
-            c->mlp_h = H;
-        }
-        const float *src[6] = {W1, b1, W2, b2, W3, b3};
-        const size_t len[6] = {(size_t)H * D, (size_t)H, (size_t)H * H, (size_t)H, (size_t)G * H, (size_t)G};
-        float *dst = c->mlp;
-        for (int i = 0; i < 6; ++i) {
-            KP_CUDA(c, cudaMemcpyAsync(dst, src[i], len[i] * 4, cudaMemcpyDefault, s));
-            dst += len[i];
-        }
-        KP_CUDA(c, cudaStreamSynchronize(s));
+    if (c->net) {
+        kmeans_mlp_destroy(c->net);
+        c->net = nullptr;
+    }
+    c->proposal = false;
+    if (!none) {
+        kmeans_mlp *net = nullptr;
+        if ((rc = kmeans_mlp_create(&net, p.D, hidden, p.G, 0, c->stream)))
+            return set_err(c, rc, "proposal network: %s", kmeans_last_error(nullptr));
+        c->net = net;
+        if ((rc = kmeans_mlp_set_params(net, W1, b1, W2, b2, W3, b3)) || (rc = mlp_prepare(net, p.N)))
+            return set_err(c, rc, "proposal network: %s", mlp_message(net));
+        if (!c->pred) KP_CUDA(c, dalloc(c, &c->pred, (size_t)p.N));
+        if (!c->cc_table) KP_CUDA(c, dalloc(c, &c->cc_table, (size_t)p.K * p.G));
+        KP_CUDA(c, cudaStreamSynchronize(c->stream));
         c->proposal = true;
     }
     if (c->graph_exec) {  // recorded with the other iteration 0
@@ -961,22 +953,16 @@ KM_API int kmeans_mlp_predict(const float *X, int64_t N, int32_t D, const float 
         return code;
     };
     if (!X || !W1 || !b1 || !W2 || !b2 || !W3 || !b3 || !pred) return fail(KM_EINVAL, "a pointer argument is NULL");
-    if (N < 1 || D < 1 || hidden < 1 || hidden > 4096 || classes < 1)
-        return fail(KM_EINVAL, "N, D, classes >= 1 and hidden in [1, 4096] required");
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int64_t chunk = std::min<int64_t>(N, (int64_t)1 << 20);
-    float *a1 = nullptr, *a2 = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&a1), (size_t)chunk * hidden * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&a2), (size_t)chunk * hidden * 4, s);
-    if (e == cudaSuccess)
-        e = launch_mlp_predict(X, N, D, W1, b1, W2, b2, W3, b3, hidden, classes, pred, a1, a2, chunk, s);
-    if (a1) cudaFreeAsync(a1, s);
-    if (a2) cudaFreeAsync(a2, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(KM_ECUDA, cudaGetErrorString(e));
-    }
-    return KM_OK;
+    if (N < 1 || D < 1 || D > 256 || hidden < 1 || hidden > 256 || classes < 1 || classes > 512)
+        return fail(KM_EINVAL, "N >= 1, D in [1, 256], hidden in [1, 256] and classes in [1, 512] required");
+    kmeans_mlp *net = nullptr;
+    int rc = kmeans_mlp_create(&net, D, hidden, classes, 0, stream);
+    if (rc) return rc;  // message already set for this thread
+    if (!rc) rc = kmeans_mlp_set_params(net, W1, b1, W2, b2, W3, b3);
+    if (!rc) rc = kmeans_mlp_predict_net(net, X, N, pred);
+    if (rc) set_thread_error(kmeans_mlp_last_error(net));
+    kmeans_mlp_destroy(net);
+    return rc;
 }
 
 KM_API const char *kmeans_last_error(const kmeans_ctx *c) { return c ? c->err : g_init_error; }

@@ -99,7 +99,9 @@ struct Params {
 
     float *C;            // K x Dp (padding columns are zero)
     double *S;           // K x D   cluster sums (FP64)
-    double *Q;           // K       sum of ||x||^2 per cluster (FP64)
+    double *Q;           // K       sum of ||x - R_k||^2 per cluster (FP64)
+    float *R;            // K x Dp  reference point of each cluster's Q (a copy of C made
+                         //         whenever the sums are rebuilt from zero)
     unsigned long long *cnt;  // K  cluster sizes
 
     float *Dc;           // tcap x K
@@ -339,9 +341,12 @@ cudaError_t launch_dense_assign(const Params &p, cudaStream_t s, int first, int 
 __host__ __device__ inline int tc_dim(int D) { return D == 32 || D == 64 ? 64 : (D == 128 ? 128 : 0); }
 bool dense_tc_eligible(const Params &p, size_t smem_limit);
 bool dense_tcb_eligible(const Params &p, size_t smem_limit);
-cudaError_t launch_mlp_predict(const float *X, int64_t N, int D, const float *W1, const float *b1, const float *W2,
-                               const float *b2, const float *W3, const float *b3, int H, int G, int32_t *pred,
-                               float *A1, float *A2, int64_t chunk, cudaStream_t s);
+// the proposal network on the tensor cores (kp_mlp.cu): buffers for N rows,
+// then the predicted class of every row, ordered on s (KM_* status)
+int mlp_prepare(kmeans_mlp *m, int64_t N);
+int mlp_predict_enqueue(kmeans_mlp *m, const float *X, int64_t N, int32_t *pred, cudaStream_t s);
+int mlp_error_flag(kmeans_mlp *m);  // synchronises; KM_ETIMEOUT if a bounded wait gave up
+const char *mlp_message(const kmeans_mlp *m);
 cudaError_t launch_proposal_seed(const Params &p, const int32_t *pred, float *T, cudaStream_t s, int respect_done,
                                  int num_sms);
 int dense_tcb_kp(const Params &p);  // padded K of the split centroid copy

@@ -320,26 +320,42 @@ __global__ void __launch_bounds__(256) k_apply_moves(Params p, int all_points, i
         const int nw = checked_label(p, n);
         if (nw < 0) continue;  // warp-uniform: one point per warp
         const float *x = p.X + n * p.D;
-        // ||x||^2 as an FP32 pair (exact squares, compensated sum): FP64
-        // arithmetic is slow on these SMs; only the atomics are FP64
-        float qh = 0.f, ql = 0.f;
+        // ||x - R_k||^2 for the new and the old cluster as FP32 pairs (exact
+        // squares, compensated sums): FP64 arithmetic is slow on these SMs;
+        // only the atomics are FP64
+        float qh = 0.f, ql = 0.f, oh = 0.f, ol = 0.f;
+        auto two_sum = [](float a, float b, float &s, float &e) {  // s + e == a + b exactly
+            s = __fadd_rn(a, b);
+            const float bb = __fsub_rn(s, a);
+            e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+        };
+        // (x - r)^2 into the pair (h, l): x - r as the exact pair dh + dl, its
+        // square as sq + sqe (exact) plus 2 dh dl + dl^2 (below 2^-47 of it)
+        auto acc = [&](float &h, float &l, float xv, float r) {
+            float dh, dl, s, e;
+            two_sum(xv, -r, dh, dl);
+            const float sq = __fmul_rn(dh, dh);
+            const float sqe = __fmaf_rn(dh, dh, -sq);
+            const float cross = __fmaf_rn(__fmul_rn(2.f, dh), dl, __fmul_rn(dl, dl));
+            two_sum(h, sq, s, e);
+            h = s;
+            l = __fadd_rn(l, __fadd_rn(e, __fadd_rn(sqe, cross)));
+        };
         for (int i = lane; i < p.D; i += 32) {
             const float xf = __ldg(x + i);
-            const float sq = __fmul_rn(xf, xf);
-            const float s = __fadd_rn(qh, sq), bb = __fsub_rn(s, qh);
-            const float e = __fadd_rn(__fsub_rn(qh, __fsub_rn(s, bb)), __fsub_rn(sq, bb));
-            ql = __fadd_rn(ql, __fadd_rn(e, __fmaf_rn(xf, xf, -sq)));
-            qh = s;
+            acc(qh, ql, xf, p.R[(size_t)nw * p.Dp + i]);
+            if (old >= 0) acc(oh, ol, xf, p.R[(size_t)old * p.Dp + i]);
             const double xi = (double)xf;
             atomicAdd(&p.S[(size_t)nw * p.D + i], xi);
             if (old >= 0) atomicAdd(&p.S[(size_t)old * p.D + i], -xi);
         }
         const double q = warp_sum_d((double)qh + (double)ql);
+        const double qo = warp_sum_d((double)oh + (double)ol);
         if (lane == 0) {
             atomicAdd(&p.Q[nw], q);
             atomicAdd(&p.cnt[nw], 1ull);
             if (old >= 0) {
-                atomicAdd(&p.Q[old], -q);
+                atomicAdd(&p.Q[old], -qo);
                 atomicAdd(&p.cnt[old], ~0ull);  // -1
             }
         }

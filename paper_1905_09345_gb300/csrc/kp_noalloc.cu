@@ -8,6 +8,8 @@
 // counts, a padded centroid copy, the control block) lives in the
 // file-scope array below, which each GPU that loads the library holds until
 // the process exits.  The paper has no counterpart to this entry point.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -42,8 +44,32 @@ constexpr size_t kScratchBytes = align256(kOffDm + sizeof(float) * 2);  // about
 // address: its device address comes from cudaGetSymbolAddress, per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// Device address of the array, per device ordinal, with the context it was
+// looked up in: a context destroyed and made again (cudaDeviceReset) loads the
+// module again, so the address is looked up again when the context differs.
+struct ScratchSlot {
+    CUcontext ctx;
+    void *ptr;
+};
 std::mutex g_mu;
-void *g_scratch_ptr[256] = {};  // device address of the array, per device ordinal
+ScratchSlot g_scratch[256] = {};
+
+// the calling thread's current context (driver entry point, fetched once)
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext *);
+    static std::once_flag once;
+    static Fn fn = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 // group table of a single group holding every centroid: gstart = {0, K}
 __global__ void k_noalloc_groups(int32_t *gstart, int K) {
@@ -102,17 +128,21 @@ KM_API int kmeans_lloyd_step_noalloc(const float *X, int64_t N, int32_t D, const
         !on_device(objective, dev))
         return fail(KM_EINVAL, "every array must be device memory of the current device");
 
-    // one-time set-up per device: the scratch array's device address
+    // set-up once per device (and again if its context was made anew): the
+    // scratch array's device address, looked up with that device current
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        const CUcontext cur = current_context();
+        if (!cur) return fail(KM_ECUDA, "no current CUDA context");
+        if (!g_scratch[dev].ptr || g_scratch[dev].ctx != cur) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) return fail(KM_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
-            g_scratch_ptr[dev] = p;
+            g_scratch[dev].ptr = p;
+            g_scratch[dev].ctx = cur;
         }
-        base = g_scratch_ptr[dev];
+        base = g_scratch[dev].ptr;
     }
     unsigned char *b = static_cast<unsigned char *>(base);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -136,6 +166,7 @@ KM_API int kmeans_lloyd_step_noalloc(const float *X, int64_t N, int32_t D, const
     p.C = reinterpret_cast<float *>(b + kOffC);
     p.S = reinterpret_cast<double *>(b + kOffS);
     p.Q = reinterpret_cast<double *>(b + kOffQ);
+    p.R = p.C;  // reference points = the centroids of this step (the update reads each before writing it)
     p.cnt = reinterpret_cast<unsigned long long *>(b + kOffCnt);
     p.Jk = reinterpret_cast<double *>(b + kOffJk);
     p.delta = reinterpret_cast<float *>(b + kOffDelta);

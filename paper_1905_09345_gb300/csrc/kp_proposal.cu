@@ -11,117 +11,12 @@
 // follows (global filter, group and point filters, distance calculator) makes
 // the labels exact whatever the prediction: a wrong guess only costs work.
 //
-// The MLP (D -> H -> H -> G, GELU, the group with the largest logit) runs in
-// FP32 on the CUDA cores: tiled GEMMs with the bias and activation fused,
-// the last layer fused with the argmax so that no logits are stored.
+// The network itself (D -> H -> H -> G, GELU, the group with the largest
+// logit) runs on the tensor cores (kp_mlp.cu).
 #include "kp_common.cuh"
 
 namespace kp {
 namespace {
-
-constexpr int kBM = 64, kBN = 64, kBK = 16;  // GEMM tile: rows x outputs x inner
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-
-// One 64 x 64 tile of  A (M x Kd, row-major) . W^T (W: Nout x Kd, row-major),
-// accumulated into acc[4][4] (thread: rows 4ty.., outputs 4tx..).
-__device__ __forceinline__ void gemm_tile(const float *A, int64_t M, int Kd, const float *W, int Nout, int64_t m0,
-                                          int j0, float (&As)[kBK][kBM + 4], float (&Ws)[kBK][kBN + 4],
-                                          float (&acc)[4][4]) {
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < Kd; k0 += kBK) {
-        // 64 x 16 of A and of W, four elements per thread, stored transposed
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int e = tid + r * 256, row = e >> 4, kk = e & 15;
-            const int64_t m = m0 + row;
-            const int k = k0 + kk, j = j0 + row;
-            As[kk][row] = (m < M && k < Kd) ? A[m * Kd + k] : 0.f;
-            Ws[kk][row] = (j < Nout && k < Kd) ? W[(int64_t)j * Kd + k] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kBK; ++kk) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-            const float4 w = *reinterpret_cast<const float4 *>(&Ws[kk][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-}
-
-// out = GELU(A W^T + b)  (M x Nout)
-__global__ void __launch_bounds__(256) k_mlp_layer(const float *A, int64_t M, int Kd, const float *W, const float *b,
-                                                   int Nout, float *out) {
-    __shared__ __align__(16) float As[kBK][kBM + 4];
-    __shared__ __align__(16) float Ws[kBK][kBN + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t m0 = (int64_t)blockIdx.x * kBM;
-    const int j0 = blockIdx.y * kBN;
-    float acc[4][4];
-    gemm_tile(A, M, Kd, W, Nout, m0, j0, As, Ws, acc);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t m = m0 + ty * 4 + i;
-        if (m >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int jj = j0 + tx * 4 + j;
-            if (jj < Nout) out[m * Nout + jj] = gelu_f(acc[i][j] + b[jj]);
-        }
-    }
-}
-
-// pred[m] = argmax_j (A W^T + b)[m][j]  (first maximum), over all Nout outputs
-__global__ void __launch_bounds__(256) k_mlp_out_argmax(const float *A, int64_t M, int Kd, const float *W,
-                                                        const float *b, int Nout, int32_t *pred) {
-    __shared__ __align__(16) float As[kBK][kBM + 4];
-    __shared__ __align__(16) float Ws[kBK][kBN + 4];
-    __shared__ float Cs[kBM][kBN + 1];
-    __shared__ float best_v[kBM];
-    __shared__ int best_i[kBM];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t m0 = (int64_t)blockIdx.x * kBM;
-    if (threadIdx.x < kBM) {
-        best_v[threadIdx.x] = -INFINITY;
-        best_i[threadIdx.x] = 0;
-    }
-    for (int j0 = 0; j0 < Nout; j0 += kBN) {
-        float acc[4][4];
-        gemm_tile(A, M, Kd, W, Nout, m0, j0, As, Ws, acc);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int jj = j0 + tx * 4 + j;
-                Cs[ty * 4 + i][tx * 4 + j] = jj < Nout ? acc[i][j] + b[jj] : -INFINITY;
-            }
-        __syncthreads();
-        if (threadIdx.x < kBM) {  // one thread per row, outputs in ascending order
-            float bv = best_v[threadIdx.x];
-            int bi = best_i[threadIdx.x];
-            for (int j = 0; j < kBN && j0 + j < Nout; ++j) {
-                const float v = Cs[threadIdx.x][j];
-                if (v > bv) {
-                    bv = v;
-                    bi = j0 + j;
-                }
-            }
-            best_v[threadIdx.x] = bv;
-            best_i[threadIdx.x] = bi;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < kBM && m0 + threadIdx.x < M) pred[m0 + threadIdx.x] = best_i[threadIdx.x];
-}
 
 // T[k][g] = min over c in group g, c != k, of a lower bound of d(c_k, c)
 // (FP32 direct difference, rounded down); +inf for a group with no such c.
@@ -222,25 +117,6 @@ __global__ void __launch_bounds__(256) k_seed(Params p, const int32_t *pred, con
 }
 
 }  // namespace
-
-cudaError_t launch_mlp_predict(const float *X, int64_t N, int D, const float *W1, const float *b1, const float *W2,
-                               const float *b2, const float *W3, const float *b3, int H, int G, int32_t *pred,
-                               float *A1, float *A2, int64_t chunk, cudaStream_t s) {
-    for (int64_t r0 = 0; r0 < N; r0 += chunk) {
-        const int64_t m = std::min(chunk, N - r0);
-        const unsigned gm = (unsigned)((m + kBM - 1) / kBM);
-        dim3 gh(gm, (unsigned)((H + kBN - 1) / kBN));
-        count_launch();
-        k_mlp_layer<<<gh, 256, 0, s>>>(X + r0 * D, m, D, W1, b1, H, A1);
-        count_launch();
-        k_mlp_layer<<<gh, 256, 0, s>>>(A1, m, H, W2, b2, H, A2);
-        count_launch();
-        k_mlp_out_argmax<<<gm, 256, 0, s>>>(A2, m, H, W3, b3, G, pred + r0);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
 
 cudaError_t launch_proposal_seed(const Params &p, const int32_t *pred, float *T, cudaStream_t s, int respect_done,
                                  int num_sms) {

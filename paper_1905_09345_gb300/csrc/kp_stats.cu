@@ -1,5 +1,5 @@
-// kp_stats.cu -- cluster statistics (S_k = sum x in FP64, Q_k = sum ||x||^2,
-// n_k) for the centroid update.
+// kp_stats.cu -- cluster statistics (S_k = sum x in FP64, Q_k = sum
+// ||x - R_k||^2 about a reference point R_k, n_k) for the centroid update.
 //
 // Two ways, chosen on the device after each assignment:
 //   * incremental (few labels changed): k_apply_moves moves each relabelled
@@ -43,6 +43,10 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_hist(Params p, int all_
     const int64_t nthr = (int64_t)gridDim.x * kStatsThreads;
     for (int64_t i = tid; i < (int64_t)K * D; i += nthr) p.S[i] = 0.0;
     for (int64_t i = tid; i < K; i += nthr) p.Q[i] = 0.0;
+    // the sums start from zero: each cluster's reference point becomes its
+    // current centroid (the one the update subtracts), so that Q_k holds the
+    // objective term itself and the update cancels nothing large
+    for (int64_t i = tid; i < (int64_t)K * p.Dp; i += nthr) p.R[i] = p.C[i];
     if (local) {
         for (int i = threadIdx.x; i < K; i += kStatsThreads) hist[i] = 0;
         __syncthreads();
@@ -154,11 +158,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // Full mode: each warp sums kSumRun consecutive sorted points, lanes over the
 // coordinates, eight points' loads in flight at a time, and adds its partial
 // sums to S and Q whenever the cluster changes along the run (and at its end).
-// FP64 arithmetic is slow on the SMs of this GPU, so the run sums are kept as
-// unevaluated FP32 pairs (hi + lo, compensated summation with TwoSum; the
-// squares split exactly with a fused multiply-add), accurate to a few units
-// in 2^-48 relative for runs this short, and turned into FP64 only when they
-// are added to the global sums.
+// Q_k sums ||x - R_k||^2 (R_k = the cluster's reference point, set to its
+// centroid by k_stats_hist).  FP64 arithmetic is slow on the SMs of this GPU,
+// so the run sums are kept as unevaluated FP32 pairs (hi + lo, compensated
+// summation with TwoSum; the squares split exactly with a fused
+// multiply-add), accurate to a few units in 2^-48 relative for runs this
+// short, and turned into FP64 only when they are added to the global sums.
 template <int NPER>  // coordinates per lane: ceil(D / 32)
 __global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respect_done) {
     Ctrl *ctrl = p.ctrl;
@@ -177,6 +182,15 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respe
         for (int j = 0; j < NPER; ++j) sh[j] = sl[j] = 0.f;
         float qh = 0.f, ql = 0.f;
         int cur = p.slab[r0];
+        float rv[NPER];  // reference point of cluster `cur`, this lane's coordinates
+        auto load_ref = [&]() {
+#pragma unroll
+            for (int j = 0; j < NPER; ++j) {
+                const int i = lane + 32 * j;
+                rv[j] = i < D ? p.R[(size_t)cur * p.Dp + i] : 0.f;
+            }
+        };
+        load_ref();
         auto flush = [&]() {
             const double qs = warp_sum_d((double)qh + (double)ql);
 #pragma unroll
@@ -213,6 +227,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respe
                 if (kb[b] != cur) {  // warp-uniform
                     flush();
                     cur = kb[b];
+                    load_ref();
                 }
 #pragma unroll
                 for (int j = 0; j < NPER; ++j) {
@@ -221,11 +236,16 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respe
                     two_sum(sh[j], xi, s, e);
                     sh[j] = s;
                     sl[j] = __fadd_rn(sl[j], e);
-                    const float sq = __fmul_rn(xi, xi);
-                    const float sqe = __fmaf_rn(xi, xi, -sq);  // exact: xi^2 == sq + sqe
+                    // x - r as an exact pair dh + dl, its square as sq + sqe (exact)
+                    // plus 2 dh dl + dl^2 (below 2^-47 of the square)
+                    float dh, dl;
+                    two_sum(xi, -rv[j], dh, dl);
+                    const float sq = __fmul_rn(dh, dh);
+                    const float sqe = __fmaf_rn(dh, dh, -sq);
+                    const float cross = __fmaf_rn(__fmul_rn(2.f, dh), dl, __fmul_rn(dl, dl));
                     two_sum(qh, sq, s, e);
                     qh = s;
-                    ql = __fadd_rn(ql, __fadd_rn(e, sqe));
+                    ql = __fadd_rn(ql, __fadd_rn(e, __fadd_rn(sqe, cross)));
                 }
             }
         }

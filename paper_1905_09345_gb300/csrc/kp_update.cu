@@ -2,11 +2,14 @@
 //
 // The update step of K-means (the centroid of each cluster becomes the mean of
 // its points; an empty cluster keeps its centroid) from FP64 cluster sums
-// S_k = sum x, Q_k = sum ||x||^2 and counts n_k, which the assignment kernels
-// keep up to date by moving each relabelled point between clusters.  The
-// objective of the assignment just made comes from the same sums,
-//   J_t = sum_k ( Q_k - 2 c_k . S_k + n_k ||c_k||^2 ),   c = C^t,
-// so no pass over X is needed.  The drift of each centroid,
+// S_k = sum x, Q_k = sum ||x - r_k||^2 and counts n_k, which the assignment
+// kernels keep up to date by moving each relabelled point between clusters
+// (r_k: the cluster's reference point, its centroid when the sums were last
+// rebuilt from zero).  The objective of the assignment just made comes from
+// the same sums: with e = c_k - r_k,
+//   J_t = sum_k ( Q_k - 2 e . (S_k - n_k r_k) + n_k ||e||^2 ),   c = C^t,
+// so no pass over X is needed, and because r_k stays near c_k no large terms
+// cancel, however far the data lie from the origin.  The drift of each centroid,
 // delta_k = ||c_k^{t+1} - c_k^t|| (rounded up), extends the cumulative drift
 // tables that the filters use to age the bounds (KPynq Sec. I: the filters
 // test bounds that must stay valid as centroids move).
@@ -35,12 +38,14 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
         const double nkd = (double)nk;
         double j1 = 0.0, j2 = 0.0, dd = 0.0;
         float *crow = p.C + (size_t)k * p.Dp;
+        const float *rrow = p.R + (size_t)k * p.Dp;
         const double *srow = p.S + (size_t)k * D;
         for (int i = lane; i < D; i += 32) {
             const float co = crow[i];
             const double s = srow[i];
-            j1 += (double)co * s;
-            j2 += (double)co * (double)co;
+            const double e = (double)co - (double)rrow[i];  // exact; read before C is written
+            j1 += e * (s - nkd * (double)rrow[i]);
+            j2 += e * e;
             if (!final_only) {
                 const float cn = nk ? (float)(s / nkd) : co;
                 const double t = (double)cn - (double)co;

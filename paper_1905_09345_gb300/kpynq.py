@@ -122,6 +122,24 @@ def lib():
         L.kmeans_batch_destroy.restype = None
         L.kmeans_batch_last_error.argtypes = [vp]
         L.kmeans_batch_last_error.restype = ctypes.c_char_p
+        u64, f32 = ctypes.c_uint64, ctypes.c_float
+        L.kmeans_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, u64, vp]
+        L.kmeans_mlp_create.restype = ctypes.c_int
+        L.kmeans_mlp_set_params.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.kmeans_mlp_set_params.restype = ctypes.c_int
+        L.kmeans_mlp_get_params.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.kmeans_mlp_get_params.restype = ctypes.c_int
+        L.kmeans_mlp_gradient.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dbl), vp]
+        L.kmeans_mlp_gradient.restype = ctypes.c_int
+        L.kmeans_mlp_train.argtypes = [vp, vp, i64, vp, i32, i64, i32, f32, u64, ctypes.POINTER(dbl),
+                                       ctypes.POINTER(dbl)]
+        L.kmeans_mlp_train.restype = ctypes.c_int
+        L.kmeans_mlp_predict_net.argtypes = [vp, vp, i64, vp]
+        L.kmeans_mlp_predict_net.restype = ctypes.c_int
+        L.kmeans_mlp_destroy.argtypes = [vp]
+        L.kmeans_mlp_destroy.restype = None
+        L.kmeans_mlp_last_error.argtypes = [vp]
+        L.kmeans_mlp_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -266,9 +284,32 @@ KM_NOALLOC_MAX_K = 1024
 KM_NOALLOC_MAX_D = 128
 
 
+def _check_tensor(name: str, a, dtype: str, shape: tuple) -> None:
+    """Raise KMeansError(KM_EINVAL) unless `a` (torch tensor or NumPy array;
+    raw addresses are passed through unchecked) has the element type, the
+    shape and a C-contiguous layout the C call reads it with."""
+    if a is None or isinstance(a, int):
+        return
+    dt = str(getattr(a, "dtype", "")).replace("torch.", "")
+    if dt != dtype:
+        raise KMeansError(KM_EINVAL, f"{name} must be {dtype}, got {dt}")
+    if tuple(a.shape) != tuple(shape):
+        raise KMeansError(KM_EINVAL, f"{name} must have shape {tuple(shape)}, got {tuple(a.shape)}")
+    contig = a.is_contiguous() if hasattr(a, "is_contiguous") else a.flags["C_CONTIGUOUS"]
+    if not contig:
+        raise KMeansError(KM_EINVAL, f"{name} must be C-contiguous")
+
+
 def kmeans_lloyd_step_noalloc(X, N: int, D: int, C, K: int, labels, C_new, objective, stream=None) -> None:
     """One plain-Lloyd iteration with no allocation (device arrays only;
-    stream-ordered, does not wait).  See include/kpynq.h."""
+    stream-ordered, does not wait).  See include/kpynq.h.  Tensors are
+    checked for type (float32 X, C, C_new; int32 labels; float64 objective),
+    shape and contiguity before the call, since the C side cannot tell."""
+    _check_tensor("X", X, "float32", (N, D))
+    _check_tensor("C", C, "float32", (K, D))
+    _check_tensor("C_new", C_new, "float32", (K, D))
+    _check_tensor("labels", labels, "int32", (N,))
+    _check_tensor("objective", objective, "float64", (1,))
     st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().kmeans_lloyd_step_noalloc(_addr(X), N, D, _addr(C), K, _addr(labels), _addr(C_new),
                                            _addr(objective), st), None)
@@ -479,6 +520,122 @@ class KMeansBatch:
         if getattr(self, "b", None):
             kmeans_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# the proposal network on the tensor cores (training and inference)
+# ---------------------------------------------------------------------------
+def _check_mlp(rc: int, m=None):
+    if rc != KM_OK:
+        msg = lib().kmeans_mlp_last_error(m).decode(errors="replace")
+        raise KMeansError(rc, msg)
+
+
+def kmeans_mlp_create(D: int, hidden: int, classes: int, seed: int = 0, stream=None):
+    m = ctypes.c_void_p()
+    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check_mlp(lib().kmeans_mlp_create(ctypes.byref(m), D, hidden, classes, seed, st), None)
+    return m.value
+
+
+def kmeans_mlp_set_params(m, W1, b1, W2, b2, W3, b3) -> None:
+    _check_mlp(lib().kmeans_mlp_set_params(m, _addr(W1), _addr(b1), _addr(W2), _addr(b2), _addr(W3), _addr(b3)), m)
+
+
+def kmeans_mlp_get_params(m, W1=None, b1=None, W2=None, b2=None, W3=None, b3=None) -> None:
+    _check_mlp(lib().kmeans_mlp_get_params(m, _addr(W1), _addr(b1), _addr(W2), _addr(b2), _addr(W3), _addr(b3)), m)
+
+
+def kmeans_mlp_gradient(m, X, y, B: int, grad) -> float:
+    """Gradient of the mean cross-entropy on the batch into ``grad``; returns the loss."""
+    loss = ctypes.c_double()
+    _check_mlp(lib().kmeans_mlp_gradient(m, _addr(X), _addr(y), B, ctypes.byref(loss), _addr(grad)), m)
+    return loss.value
+
+
+def kmeans_mlp_train(m, X, N: int, labels, K: int, steps: int, batch: int, lr: float, seed: int):
+    """Adam steps on rows drawn from (X, labels); returns (mean loss, accuracy) over the steps."""
+    loss, acc = ctypes.c_double(), ctypes.c_double()
+    _check_mlp(lib().kmeans_mlp_train(m, _addr(X), N, _addr(labels), K, steps, batch, lr, seed,
+                                      ctypes.byref(loss), ctypes.byref(acc)), m)
+    return loss.value, acc.value
+
+
+def kmeans_mlp_predict_net(m, X, N: int, pred) -> None:
+    _check_mlp(lib().kmeans_mlp_predict_net(m, _addr(X), N, _addr(pred)), m)
+
+
+def kmeans_mlp_destroy(m) -> None:
+    if m:
+        lib().kmeans_mlp_destroy(m)
+
+
+def kmeans_mlp_last_error(m=None) -> str:
+    return lib().kmeans_mlp_last_error(m).decode(errors="replace")
+
+
+class MLP:
+    """The proposal network D -> hidden -> hidden -> classes (GELU), trained
+    and evaluated on the tensor cores.  Parameters are exchanged as FP32
+    arrays with O3's names and shapes (W1 hidden x D, b1, W2, b2, W3 classes x
+    hidden, b3)."""
+
+    def __init__(self, D: int, hidden: int, classes: int, seed: int = 0, stream=None):
+        self.D, self.H, self.G = D, hidden, classes
+        self.m = kmeans_mlp_create(D, hidden, classes, seed, stream)
+
+    def shapes(self) -> dict:
+        D, H, G = self.D, self.H, self.G
+        return {"W1": (H, D), "b1": (H,), "W2": (H, H), "b2": (H,), "W3": (G, H), "b3": (G,)}
+
+    def n_params(self) -> int:
+        n = 0
+        for shp in self.shapes().values():
+            k = 1
+            for v in shp:
+                k *= v
+            n += k
+        return n
+
+    def split(self, vec) -> dict:
+        """A flat parameter-layout vector as a dict of views with O3's names."""
+        out, o = {}, 0
+        for k, shp in self.shapes().items():
+            n = 1
+            for v in shp:
+                n *= v
+            out[k] = vec[o:o + n].reshape(shp)
+            o += n
+        return out
+
+    def set_params(self, params: dict) -> None:
+        w = [params[k] for k in MLP_NAMES]
+        kmeans_mlp_set_params(self.m, *w)
+
+    def get_params(self, out: dict) -> dict:
+        kmeans_mlp_get_params(self.m, *[out[k] for k in MLP_NAMES])
+        return out
+
+    def gradient(self, X, y, grad) -> float:
+        return kmeans_mlp_gradient(self.m, X, y, X.shape[0], grad)
+
+    def train(self, X, labels, K: int, steps: int, batch: int = 8192, lr: float = 1e-3, seed: int = 1):
+        return kmeans_mlp_train(self.m, X, X.shape[0], labels, K, steps, batch, lr, seed)
+
+    def predict(self, X, pred):
+        kmeans_mlp_predict_net(self.m, X, X.shape[0], pred)
+        return pred
+
+    def close(self):
+        if getattr(self, "m", None):
+            kmeans_mlp_destroy(self.m)
+            self.m = None
 
     def __del__(self):
         try:

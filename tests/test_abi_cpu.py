@@ -120,7 +120,7 @@ def test_null_context_calls(L):
     assert lib.kmeans_mlp_predict(None, 10, 4, None, None, None, None, None, None, 8, 3, None, None) == L.KM_EINVAL
     fake = 16  # any non-NULL address: the size checks come first
     assert lib.kmeans_mlp_predict(fake, 0, 4, fake, fake, fake, fake, fake, fake, 8, 3, fake, None) == L.KM_EINVAL
-    assert lib.kmeans_mlp_predict(fake, 10, 4, fake, fake, fake, fake, fake, fake, 5000, 3, fake, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_predict(fake, 10, 4, fake, fake, fake, fake, fake, fake, 300, 3, fake, None) == L.KM_EINVAL
     assert "hidden" in L.kmeans_last_error(None)
     lib.kmeans_selftest_sqrt.restype = __import__("ctypes").c_int
     assert lib.kmeans_selftest_sqrt(None) == L.KM_EINVAL
@@ -129,3 +129,44 @@ def test_null_context_calls(L):
 def test_default_options(L):
     o = L.kmeans_default_options()
     assert o.algo == L.KM_ALGO_FILTERED and o.grouping == L.KM_GROUP_CONTIGUOUS and not o.stream
+
+
+def test_mlp_entry_points_reject_bad_arguments(L):
+    """The proposal network's entry points check sizes and pointers before any
+    device work."""
+    lib = L.lib()
+    out = ctypes.c_void_p()
+    for D, H, G in ((0, 8, 4), (257, 8, 4), (8, 0, 4), (8, 257, 4), (8, 8, 0), (8, 8, 513)):
+        assert lib.kmeans_mlp_create(ctypes.byref(out), D, H, G, 0, None) == L.KM_EINVAL, (D, H, G)
+        assert out.value is None
+        assert "range" in L.kmeans_mlp_last_error(None)
+    assert lib.kmeans_mlp_create(None, 8, 8, 4, 0, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_set_params(None, None, None, None, None, None, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_get_params(None, None, None, None, None, None, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_gradient(None, None, None, 128, None, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_train(None, None, 1, None, 0, 1, 128, 1e-3, 1, None, None) == L.KM_EINVAL
+    assert lib.kmeans_mlp_predict_net(None, None, 1, None) == L.KM_EINVAL
+    lib.kmeans_mlp_destroy(None)
+
+
+def test_noalloc_wrapper_checks_types_and_shapes(L):
+    """kmeans_lloyd_step_noalloc's Python wrapper refuses arrays whose element
+    type, shape or layout the C call would misread."""
+    import numpy as np
+    N, D, K = 100, 8, 4
+    X = np.zeros((N, D), np.float32)
+    C = np.zeros((K, D), np.float32)
+    lab = np.zeros(N, np.int32)
+    J = np.zeros(1, np.float64)
+    bad = [
+        dict(X=X.astype(np.float64)), dict(C=C.astype(np.float64)), dict(C_new=np.zeros((K, D + 1), np.float32)),
+        dict(labels=lab.astype(np.int64)), dict(objective=np.zeros(1, np.float32)),
+        dict(X=np.zeros((D, N), np.float32).T),  # not C-contiguous
+    ]
+    for b in bad:
+        args = dict(X=X, C=C, labels=lab, C_new=np.zeros((K, D), np.float32), objective=J)
+        args.update(b)
+        with pytest.raises(L.KMeansError) as e:
+            L.kmeans_lloyd_step_noalloc(args["X"], N, D, args["C"], K, args["labels"], args["C_new"],
+                                        args["objective"])
+        assert e.value.status == L.KM_EINVAL, b

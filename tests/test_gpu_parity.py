@@ -233,6 +233,24 @@ def test_tensor_core_near_ties(kp, D):
         assert st[0]["n_recheck"] > 0
 
 
+@pytest.mark.parametrize("algo", [0, 1], ids=["filtered", "lloyd"])
+@pytest.mark.parametrize("offset", [1e4, 1e5])
+def test_objective_far_from_origin(kp, offset, algo):
+    """Unit-spread blobs shifted by a large common offset (raw features are
+    often far from the origin): the objective comes from per-cluster sums, and
+    must still agree with the oracle's direct FP64 sum of squared distances
+    within 1e-9 relative in every iteration (the lockstep check).  Summed
+    about the origin, ||x||^2 / J per point is ~1e8-1e10 here, which a
+    48-bit partial sum would turn into a relative error of up to ~1e-5."""
+    rng = np.random.default_rng(int(offset) // 1000 + 7 * algo)
+    N, D, K = 8192, 64, 32
+    X, _ = synth.gaussian_mixture(rng, N, D, K, centre_range=10.0, scale="fixed", scale_args=(1.0,))
+    X = (X.astype(np.float64) + offset).astype(np.float32)
+    C0 = synth.sample_init(rng, X, K)
+    st = lockstep(kp, X, C0, 4, 6, algo=algo)
+    assert all(s["objective"] < 200.0 * N * D for s in st)  # J is O(N D centre_range^2), not O(N D offset^2)
+
+
 def test_bounds_stay_valid(kp):
     w = synth.small_blobs(N=3000, D=16, K=24, G=5, seed=4)
     lockstep(kp, w.X, w.C0, w.G, 12, check_bounds=True, dense_switch=1.0)

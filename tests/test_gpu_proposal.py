@@ -1,8 +1,7 @@
 """The learned group proposal (kmeans_set_proposal, kmeans_mlp_predict).
 
-* The GPU MLP's predictions equal O3's (FP64) wherever O3's two largest
-  logits are apart by more than FP32 rounding can bridge; elsewhere the GPU
-  picks one of the near-maximal groups.
+* (The network's own checks against O3 -- gradients, Adam, predictions --
+  are in test_gpu_mlp.py.)
 * A seeded iteration 0 keeps the filtered method exact: with a trained
   proposal, a random one and a deliberately wrong one, every fit equals the
   fit without a proposal (iterations, labels, objective) and its final
@@ -31,31 +30,6 @@ def kp():
 
 def _dev_params(params):
     return {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda() for k, v in params.items()}
-
-
-def test_mlp_predict_matches_oracle(kp):
-    rng = np.random.default_rng(3)
-    N, D, H, G = 5003, 32, 64, 40
-    params = mlp.init_params(D, H, G, seed=7)
-    for k in ("b1", "b2", "b3"):
-        params[k] = rng.normal(0, 0.2, params[k].shape)
-    params32 = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
-    X = rng.normal(0, 2.0, (N, D)).astype(np.float32)
-    dp = _dev_params(params)
-    pred = torch.empty(N, dtype=torch.int32, device="cuda")
-    kp.kmeans_mlp_predict(torch.from_numpy(X).cuda(), N, D, *[dp[k] for k in kp.MLP_NAMES], H, G, pred)
-    torch.cuda.synchronize()
-    got = pred.cpu().numpy()
-    logits, _ = mlp.forward(params32, X.astype(np.float64))
-    ref = np.argmax(logits, axis=1)
-    srt = np.sort(logits, axis=1)
-    margin = srt[:, -1] - srt[:, -2]
-    scale = np.abs(logits).max(axis=1) + 1.0
-    clear = margin > 1e-4 * scale
-    assert clear.mean() > 0.99
-    assert np.array_equal(got[clear], ref[clear])
-    near = logits[np.arange(N), got] >= srt[:, -1] - 1e-4 * scale
-    assert near.all()
 
 
 def _problem(seed=0, N=20000, D=32, K=256, G=26):

@@ -9,7 +9,8 @@ row through the C ABI (the second call starting from the first call's
 centroids, so the shared scratch is reused) and each call is checked against
 ``kmeans_iterate`` on a plain-Lloyd context at the same centroids: labels
 exactly, centroids within the parity tolerance (1e-5 relative), objective
-within 1e-9 relative.  This file is collected last on purpose.
+within 1e-9 relative -- and against the FP64 oracle's assignment and update
+(O1) from the same centroids.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -36,7 +37,8 @@ def _data(N=20000, D=24, K=40, seed=11):
 
 
 @pytest.mark.gpu
-def test_noalloc_step_matches_iterate_twice(kp):
+def test_noalloc_step_matches_iterate_twice(kp, oracle_lib):
+    oracle = oracle_lib
     X, C0 = _data()
     N, D = X.shape
     K = C0.shape[0]
@@ -60,6 +62,13 @@ def test_noalloc_step_matches_iterate_twice(kp):
         b = ref_C.cpu().numpy().astype(np.float64)
         assert np.abs(a - b).max() <= CENTROID_RTOL * max(1.0, np.abs(b).max()), f"call {call}"
         assert abs(J.item() - st["objective"]) <= OBJECTIVE_RTOL * st["objective"], f"call {call}"
+        # the FP64 oracle from the same centroids: exact labels, means, J
+        Cin = C.cpu().numpy().astype(np.float64)
+        o_lab, _, _, _ = oracle.lloyd_assign(X, Cin)
+        o_C, _, o_J = oracle.lloyd_update(X, o_lab, Cin)
+        assert np.array_equal(labels.cpu().numpy(), o_lab), f"call {call}: labels differ from the oracle"
+        assert np.abs(a - o_C).max() <= CENTROID_RTOL * max(1.0, np.abs(o_C).max()), f"call {call}"
+        assert abs(J.item() - o_J) <= OBJECTIVE_RTOL * o_J, f"call {call}: {J.item()} vs {o_J}"
         C = C_new.clone()
     km.close()
 
