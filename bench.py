@@ -63,7 +63,10 @@ def parse():
                     help="run only the profiled pass (every kernel launched eagerly, timed with CUDA "
                          "events) and print its breakdown: the command the ncu launch list is taken on")
     ap.add_argument("--n", type=int, default=None, help="points (default: the full workload)")
-    ap.add_argument("--train-epochs", type=int, default=3, help="proposal workload: MLP training epochs (host)")
+    ap.add_argument("--train-steps", type=int, default=3000,
+                    help="proposal workload: Adam steps (8192 rows each) of the GPU trainer")
+    ap.add_argument("--train-n", type=int, default=1 << 20,
+                    help="proposal workload: points per training seed (8 seeds)")
     return ap.parse_args()
 
 
@@ -712,94 +715,136 @@ def run_gsweep(args):
 
 
 def run_proposal(args):
-    """The learned-proposal family: an MLP (O3, FP64, trained on the host on a
-    sample of training seed 1, labelled with the groups of that seed's final
-    centroids) seeds iteration 0 of held-out seed 9; fits with and without it."""
+    """The learned-proposal family (N=8,388,608, D=32, K=4096, G=410, 40
+    iterations).  The network D -> 256 -> 256 -> G is trained on the GPU
+    (kmeans_mlp_train: tcgen05 forward and backward, Adam) on (point, group of
+    its final centroid) pairs from the library's own fits of training seeds
+    1..8 of the family, then seeds iteration 0 of fits of the held-out seed 9;
+    fits with and without it."""
     import numpy as np
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    from oracle import mlp
     from paper_1905_09345_gb300 import kpynq, synth
-    dev = torch.device("cuda", local)
+    rec = proposal_record(args, torch.device("cuda", local), log=lambda *a: print(*a, file=sys.stderr, flush=True)
+                          if rank == 0 else None)
+    if rank != 0:
+        return
+    line = {"metric": "points*iters/s (filtered K-means seeded by the learned proposal, exact labels)",
+            "value": rec["with_proposal"]["points_iters_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["with_proposal"]["ms_per_fit"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    line.update(rec)
+    print(json.dumps(line), flush=True)
+
+
+def proposal_record(args, dev, log=None, steps=None, warmup=None):
+    import numpy as np
+    import torch
+    from paper_1905_09345_gb300 import kpynq, synth
+    log = log or (lambda *a: None)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     stream = torch.cuda.current_stream(dev)
     N = args.n or 1 << 23
     H = 256
-    log = lambda *a: print(*a, file=sys.stderr, flush=True) if rank == 0 else None
-    # training labels: the groups of the final centroids of a fit on seed 1
-    wt = synth.proposal_family(1, N=N)
-    G, K = wt.G, wt.K
-    km = kpynq.KMeans(torch.from_numpy(wt.X).to(dev), torch.from_numpy(wt.C0).to(dev), G, stream=stream)
-    lab = torch.empty(wt.N, dtype=torch.int32, device=dev)
-    km.fit(wt.max_iter, wt.tol, lab, with_stats=False)
-    km.close()
-    grp = (np.arange(K, dtype=np.int64) * G) // K
-    ntrain = min(wt.N, 1 << 16)
-    y = grp[lab[:ntrain].cpu().numpy()]
+    n_train = args.train_n
+    # training pairs: the groups of the final labels of fits on seeds 1..8
     t0 = time.perf_counter()
-    params = mlp.train(wt.X[:ntrain], y, hidden=H, classes=G, seed=1, epochs=args.train_epochs, batch=8192,
-                       lr=1e-3)
-    train_s = time.perf_counter() - t0
-    log(f"[proposal] trained on {ntrain} points x {args.train_epochs} epochs in {train_s:.1f} s")
-    del wt
+    Xs, labs = [], []
+    for seed in range(1, 9):
+        wt = synth.proposal_family(seed, N=n_train)
+        Xd = torch.from_numpy(wt.X).to(dev)
+        km = kpynq.KMeans(Xd, torch.from_numpy(wt.C0).to(dev), wt.G, stream=stream)
+        lab = torch.empty(wt.N, dtype=torch.int32, device=dev)
+        km.fit(wt.max_iter, wt.tol, lab, with_stats=False)
+        km.close()
+        Xs.append(Xd)
+        labs.append(lab)
+    G, K, D = wt.G, wt.K, wt.D
+    Xtr = torch.cat(Xs)
+    ytr = torch.cat(labs)
+    del Xs, labs
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    net = kpynq.MLP(D, H, G, seed=1, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    train_loss, train_acc = net.train(Xtr, ytr, K, steps=args.train_steps, batch=8192, lr=1e-3, seed=7)
+    e1.record(stream)
+    e1.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    per_sample = 2.0 * 3.0 * (D * H + H * H + H * G)  # forward + backward flops per row
+    train_tflops = args.train_steps * 8192 * per_sample / (train_ms / 1e3) / 1e12
+    log(f"[proposal] trained {args.train_steps} steps x 8192 rows on {Xtr.shape[0]} pairs in {train_ms:.0f} ms "
+        f"(loss {train_loss:.3f}, batch accuracy {train_acc:.3f})")
+    params = net.get_params({k: torch.empty(shp, dtype=torch.float32, device=dev)
+                             for k, shp in net.shapes().items()})
+    del Xtr, ytr
     # held-out seed 9
     w = synth.proposal_family(9, N=N)
     X = torch.from_numpy(w.X).to(dev)
     C0 = torch.from_numpy(w.C0).to(dev)
     lab = torch.empty(w.N, dtype=torch.int32, device=dev)
-    dparams = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev) for k, v in params.items()}
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
+    final_groups = None
     with ClockSampler(gpu_uuid()) as clk:
         for name in ("without", "with"):
             km = kpynq.KMeans(X, C0, G, stream=stream)
             if name == "with":
-                km.set_proposal(dparams)
+                km.set_proposal(params)
             times, iters = [], []
-            for i in range(args.warmup + args.steps):
+            for i in range(warmup + steps):
                 flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
                 km.reset(C0)
                 r = km.fit(w.max_iter, w.tol, lab, with_stats=False)
-                e1.record(stream)
-                e1.synchronize()
-                if i >= args.warmup:
-                    times.append(e0.elapsed_time(e1))
+                b.record(stream)
+                b.synchronize()
+                if i >= warmup:
+                    times.append(a.elapsed_time(b))
                     iters.append(r.n_iter)
             st = km.stats(0, iters[-1])
+            km.close()
             prof = kpynq.KMeans(X, C0, G, stream=stream, profile=True)
             if name == "with":
-                prof.set_proposal(dparams)
+                prof.set_proposal(params)
             prof.fit(w.max_iter, w.tol, lab)
             breakdown = {k: v for k, v in prof.profile().items() if v[0]}
             prof.close()
-            labels = lab.cpu().numpy()
-            km.close()
+            if name == "without":
+                final_groups = (lab.to(torch.int64) * G) // K
             ms = statistics.mean(times)
             out[name] = {"ms_per_fit": ms, "iters": iters[-1],
                          "points_iters_per_s": w.N * statistics.mean(iters) / (ms / 1e3),
-                         "iter0": {k: st[0][k] for k in ("path", "n_dist", "n_survivors", "n_recheck")},
+                         "iter0": {k: st[0][k] for k in ("path", "n_dist", "n_survivors", "n_settle", "n_recheck")},
+                         "n_recheck_total": int(sum(s_["n_recheck"] for s_ in st)),
                          "skip_fraction": 1.0 - sum(s_["n_dist"] for s_ in st) / (w.N * K * len(st)),
                          "profile_ms": {k: round(v[1], 3) for k, v in breakdown.items()}}
-            if name == "without":
-                final_groups = grp[labels]
     pred = torch.empty(w.N, dtype=torch.int32, device=dev)
-    kpynq.kmeans_mlp_predict(X, w.N, w.D, *[dparams[k] for k in kpynq.MLP_NAMES], H, G, pred, stream)
-    acc = float((pred.cpu().numpy() == final_groups).mean())
-    if rank != 0:
-        return
-    line = {"metric": "points*iters/s (filtered K-means seeded by the learned proposal, exact labels)",
-            "value": out["with"]["points_iters_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": out["with"]["ms_per_fit"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "N": w.N, "D": w.D, "K": K, "G": G, "hidden": H,
-                       "train": f"O3 (FP64, host) on {ntrain} points of seed 1, {args.train_epochs} epochs, "
-                                f"{train_s:.1f} s", "l2": "flushed between steps"},
-            "clocks": clk.summary(), "proposal_accuracy": acc, "with_proposal": out["with"],
-            "without_proposal": out["without"],
-            "vs_without": out["with"]["points_iters_per_s"] / out["without"]["points_iters_per_s"]}
-    print(json.dumps(line), flush=True)
+    net.predict(X, pred)
+    acc = float((pred.to(torch.int64) == final_groups).float().mean().item())
+    net.close()
+    inf_flops = 2.0 * w.N * (D * H + H * H + H * G)
+    prop_ms = out["with"]["profile_ms"].get("proposal")
+    rec = {"config": {"workload": w.name, "N": w.N, "D": D, "K": K, "G": G, "hidden": H,
+                      "train": f"GPU (kmeans_mlp_train, tcgen05 BF16 products, FP32 Adam): {args.train_steps} "
+                               f"steps x 8192 rows drawn from {8 * n_train} (point, final group) pairs of "
+                               f"training seeds 1-8 ({n_train} points each), lr 1e-3",
+                      "l2": "flushed between steps"},
+           "clocks": clk.summary(),
+           "train": {"ms": train_ms, "steps": args.train_steps, "batch": 8192, "mean_loss": train_loss,
+                     "batch_accuracy": train_acc, "tflops": train_tflops, "prep_s": prep_s},
+           "proposal_accuracy": acc,
+           "mlp_inference": {"flops": inf_flops,
+                             "proposal_kernels_ms": prop_ms,
+                             "tflops_upper": (inf_flops / (prop_ms / 1e3) / 1e12) if prop_ms else None,
+                             "note": "proposal_kernels_ms also holds the centroid table and the seeded bounds"},
+           "with_proposal": out["with"], "without_proposal": out["without"],
+           "vs_without": out["with"]["points_iters_per_s"] / out["without"]["points_iters_per_s"]}
+    return rec
 
 
 def main():

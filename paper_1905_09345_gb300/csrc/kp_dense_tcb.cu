@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float c2max = __fmul_ru(*c2max_s, 1.0f + 1.0f / 1024);
         const float cmax = sqrt_hi(c2max);
         const float ec2 = __fmul_ru(cfg.e_c2, c2max);
+        const bool bounds = p.algo == KM_ALGO_FILTERED;  // plain Lloyd keeps no bounds
         const int wrow = (warp - 2) * 32;      // this warp's rows in the staging area
         float *row = stage + (size_t)(wrow + lane) * cfg.srow;
         const uint32_t row_addr = smem_u32(row);
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float *st0 = stage + (size_t)wrow * cfg.srow;
                 for (int e = lane; e < rows * cnt; e += 32) {
                     const int rw = e / cnt, s = e - rw * cnt;
-                    if (gfirst + s < G) p.lb[(n0 + rw) * p.Gp + gfirst + s] = st0[rw * cfg.srow + s];
+                    if (bounds && gfirst + s < G) p.lb[(n0 + rw) * p.Gp + gfirst + s] = st0[rw * cfg.srow + s];
                 }
                 __syncwarp();
                 gfirst += cnt;
@@ -350,11 +351,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!need) p.label[n] = best;
                 // the winner's group excludes the winner: every other column is
                 // at least the runner-up; the smallest group bound is that bound
-                const float lw = b2 == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, b2), E));
-                p.lb[n * p.Gp + group_of(bm, best)] = lw;
-                p.lbg[n] = lw;
-                p.u[n] = sqrt_hi(__fadd_ru(__fadd_ru(xup, b1), E));
-                p.stamp[n] = make_stamp(v, v);
+                if (bounds) {
+                    const float lw = b2 == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, b2), E));
+                    p.lb[n * p.Gp + group_of(bm, best)] = lw;
+                    p.lbg[n] = lw;
+                    p.u[n] = sqrt_hi(__fadd_ru(__fadd_ru(xup, b1), E));
+                    p.stamp[n] = make_stamp(v, v);
+                }
             }
             {
                 const bool moved = valid && !need && old != best;
@@ -427,7 +430,7 @@ __global__ void k_split_c(Params p, int Kp, int respect_done, int if_dense) {
 
 bool plan_b(const Params &p, size_t smem_limit, TcbCfg &cfg, size_t &smem) {
     const int Dt = tc_dim(p.D);
-    if (!Dt || p.K <= 256 || p.algo != KM_ALGO_FILTERED) return false;
+    if (!Dt || p.K <= 256) return false;
     cfg.Kp = ((p.K + kNB - 1) / kNB) * kNB;
     if (cfg.Kp > kMaxKp) return false;
     cfg.nb = cfg.Kp / kNB;

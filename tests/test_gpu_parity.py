@@ -50,14 +50,12 @@ def get_labels(km):
 
 def tc_expected(D, K, G, smem=232448, algo=0):
     """Mirror of the tensor-core kernels' eligibility (shape and shared memory):
-    one accumulator block for K <= 256, streamed centroid blocks above (the
-    filtered method only)."""
+    one accumulator block for K <= 256, streamed centroid blocks above (both
+    the filtered method and plain Lloyd)."""
     Dt = {32: 64, 64: 64, 128: 128}.get(D)  # operand copies zero-padded to 64 / 128
     if Dt is None:
         return False
     if K > 256:
-        if algo != 0:
-            return False
         Kp = (K + 127) // 128 * 128
         if Kp > 4096:
             return False
@@ -202,7 +200,9 @@ def test_edge_shapes_lockstep(kp, N, D, K, G, iters, dense):
              dense_switch=1.0 if dense else 0.0)
 
 
-LLOYD_SHAPES = EDGE[:6] + [(5000, 64, 256, 26, 4), (3001, 32, 33, 4, 5)]
+LLOYD_SHAPES = EDGE[:6] + [(5000, 64, 256, 26, 4), (3001, 32, 33, 4, 5),
+                           # K > 256: streamed centroid blocks on the tensor cores
+                           (5000, 64, 300, 30, 3), (3001, 128, 600, 60, 3), (4000, 32, 1024, 103, 2)]
 
 
 @pytest.mark.parametrize("dense", [0, 1], ids=["auto", "fp32"])
