@@ -28,8 +28,10 @@ K = N zero objective), a hand-derived worked example (``tests/golden``),
 scipy ``cdist`` and scikit-learn's Lloyd as independent library routines,
 Lloyd invariants (monotone objective, fixed point), exact tie cases, O2 == O1
 label-for-label every iteration (under contiguous, clustered, random and
-partly empty groupings), O2 bound validity, the clustered grouping's fixed
-point and degenerate cases, and planted mistakes that the pins must catch.
+partly empty groupings), O2 bound validity, O2's per-iteration skip counters
+against hand-derived traces (``tests/golden/o2_filter_counts.json``), the
+clustered grouping's fixed point and degenerate cases, and planted mistakes
+that the pins must catch (one per skip counter among them).
 """
 from __future__ import annotations
 

@@ -272,6 +272,33 @@ def check_ti_golden(lib_ti=None):
     return bad
 
 
+COUNTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "o2_filter_counts.json")
+
+
+def check_ti_counts(lib_ti=None):
+    """O2's per-iteration filter counters against hand-derived traces (the
+    derivation of every count is written in the fixture)."""
+    bad = []
+    for case in json.load(open(COUNTS))["cases"]:
+        X = np.array(case["X"], np.float64)
+        C0 = np.array(case["C0"], np.float64)
+        r = oracle.ti_fit(X, C0, case["G"], case["max_iter"], case["tol"], lib=lib_ti)
+        nm = case["name"]
+        if r["n_iter"] != case["n_iter"]:
+            bad.append(f"{nm}: n_iter {r['n_iter']}")
+            continue
+        got = r["cnt_hist"].tolist()
+        if got != case["cnt_hist"]:
+            bad.append(f"{nm}: counters {got} != {case['cnt_hist']}")
+        if "labels" in case and list(r["labels"]) != case["labels"]:
+            bad.append(f"{nm}: labels {r['labels']}")
+        if "J_hist" in case and not np.allclose(r["J_hist"], case["J_hist"], rtol=1e-13, atol=1e-12):
+            bad.append(f"{nm}: J_hist {r['J_hist']}")
+        if "centroids" in case and not np.allclose(r["centroids"], case["centroids"], rtol=1e-14, atol=1e-14):
+            bad.append(f"{nm}: centroids")
+    return bad
+
+
 def check_ti_init_bounds_exact(lib_ti=None):
     """After iteration 0 the bounds are exact by definition: u = d(x, c_a) and
     lb_g = min over c in g, c != a of d(x, c) (+inf if g holds only a)."""
@@ -322,6 +349,10 @@ def test_o2_golden(oracle_lib):
     assert check_ti_golden() == []
 
 
+def test_o2_counters_hand_derived(oracle_lib):
+    assert check_ti_counts() == []
+
+
 def test_o2_init_bounds_exact(oracle_lib):
     assert check_ti_init_bounds_exact() == []
 
@@ -355,6 +386,19 @@ TI_MUTANTS = [
     ("init bound includes label", [("if (k != best && sqrt(s[k]) < row[grp[k]])", "if (sqrt(s[k]) < row[grp[k]])")]),
     ("tie in scan to later index", [("(sc == bs && c < best)", "(sc == bs && c > best)")]),
     ("filter on squared vs root", [("if (beyond(m, ub)) {", "if (beyond(m * m, ub)) {")]),
+    # the skip counters (one plausible bookkeeping mistake each)
+    ("tight counted as global", [("cnt[CNT_TIGHT] += 1;", "cnt[CNT_GLOBAL] += 1;")]),
+    ("global filter not counted", [("cnt[CNT_GLOBAL] += 1;", "")]),
+    ("group filter counted when scanning",
+     [("cnt[CNT_GROUP] += 1;\n                continue;\n            }\n            scanned[g] = 1;",
+       "continue;\n            }\n            scanned[g] = 1;\n            cnt[CNT_GROUP] += 1;")]),
+    ("point filter counted after the distance",
+     [("cand[c] = bound;\n                    cnt[CNT_POINT] += 1;", "cand[c] = bound;"),
+      ("cnt[CNT_DIST] += 1;\n                cand[c] = sqrt(sc);",
+       "cnt[CNT_DIST] += 1;\n                cnt[CNT_POINT] += 1;\n                cand[c] = sqrt(sc);")]),
+    ("tightening not counted as a distance", [("double da = sqrt(sa);\n        cnt[CNT_DIST] += 1;", "double da = sqrt(sa);")]),
+    ("every scanned point counted as changed", [("if (best != al) cnt[CNT_CHANGED] += 1;", "cnt[CNT_CHANGED] += 1;")]),
+    ("iteration 0 counts K - 1 distances", [("cnt[CNT_DIST] += K;", "cnt[CNT_DIST] += K - 1;")]),
 ]
 
 
@@ -371,5 +415,5 @@ def test_planted_mistake_in_o1_is_caught(tmp_path, oracle_lib, name, repl):
 def test_planted_mistake_in_o2_is_caught(tmp_path, oracle_lib, name, repl):
     lib = oracle.compile_variant("ti", repl, str(tmp_path))
     failures = (check_ti_equals_lloyd(lib_ti=lib) + check_ti_bounds(lib_ti=lib) + check_ti_skips(lib_ti=lib)
-                + check_ti_golden(lib_ti=lib) + check_ti_init_bounds_exact(lib_ti=lib))
+                + check_ti_golden(lib_ti=lib) + check_ti_init_bounds_exact(lib_ti=lib) + check_ti_counts(lib_ti=lib))
     assert failures, f"no pin caught the planted mistake: {name}"
