@@ -1,0 +1,137 @@
+"""Parity at the full sizes of the high-dimension, learned-proposal and
+batched workloads, in the configuration the benchmark runs them.
+
+The oracle cannot assign millions of points to a thousand centroids every
+iteration within a test, so each checked iteration compares the GPU's labels
+with O1's FP64 argmin on a seeded random sample of 65,536 points (bit for
+bit), and checks the update and the objective over all points: O1's means of
+the GPU's labels (1e-5 relative) and O1's J of those labels at the GPU's
+centroids (1e-9 relative).  Two iterations are checked this way; the fit then
+runs to its stop rule, and its final labels (sampled) and objective (exact)
+are checked against the returned centroids.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1905_09345_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+CENTROID_RTOL = 1e-5
+OBJECTIVE_RTOL = 1e-9
+SAMPLE = 1 << 16
+
+
+@pytest.fixture(scope="module")
+def kp():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1905_09345_gb300 import build, kpynq
+    build.build()
+    oracle.build()
+    return kpynq
+
+
+def _C(km):
+    out = torch.empty(km.K, km.D, dtype=torch.float32, device="cuda")
+    return km.centroids(out).cpu().numpy().astype(np.float64)
+
+
+def _labels(km):
+    out = torch.empty(km.N, dtype=torch.int32, device="cuda")
+    return km.labels(out).cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def sampled_run(kp, km, X64, max_iter, tol, seed):
+    N = X64.shape[0]
+    rng = np.random.default_rng(seed)
+    prev = None
+    for t in range(2):
+        Ct = _C(km)
+        st = km.iterate()
+        lab = _labels(km)
+        idx = rng.choice(N, SAMPLE, replace=False)
+        ref, _, _, _ = oracle.lloyd_assign(X64[idx], Ct)
+        bad = np.flatnonzero(lab[idx] != ref)
+        assert bad.size == 0, f"t={t}: {bad.size} sampled labels differ"
+        if prev is not None:
+            assert st["n_changed"] == int((lab != prev).sum())
+        Cn_ref, _, J = oracle.lloyd_update(X64, lab, Ct)
+        assert _rel(_C(km), Cn_ref) <= CENTROID_RTOL, t
+        assert abs(st["objective"] - J) <= OBJECTIVE_RTOL * J, (t, st["objective"], J)
+        prev = lab
+    labt = torch.empty(km.N, dtype=torch.int32, device="cuda")
+    Ct = torch.empty(km.K, km.D, device="cuda")
+    r = km.fit(max_iter - 2, tol, labt, Ct)
+    lab = labt.cpu().numpy()
+    C = Ct.cpu().numpy().astype(np.float64)
+    idx = rng.choice(N, SAMPLE, replace=False)
+    ref, _, _, _ = oracle.lloyd_assign(X64[idx], C)
+    assert np.array_equal(lab[idx], ref)
+    J = oracle.lloyd_objective(X64, lab, C)
+    assert abs(r.objective - J) <= OBJECTIVE_RTOL * J
+    return r
+
+
+@pytest.mark.parametrize("algo", [0, 1], ids=["filtered", "lloyd"])
+def test_highdim_4m_full_size(kp, algo):
+    """N=4,194,304, D=128, K=1024, G=103, stored as bfloat16 (the library
+    widens it exactly), 30 iterations: the filtered method and plain Lloyd,
+    both with tensor-core dense passes."""
+    w = synth.highdim_4m()
+    Xb = torch.from_numpy(synth.bf16_bits(w.X).view(np.int16)).view(torch.bfloat16).cuda()
+    km = kp.KMeans(Xb, torch.from_numpy(w.C0).cuda(), w.G, algo=algo)
+    r = sampled_run(kp, km, w.X.astype(np.float64), w.max_iter, w.tol, seed=3)
+    assert any(s["path"] == kp.KM_PATH_DENSE_TC for s in r.stats)
+    km.close()
+
+
+def test_proposal_family_full_size(kp):
+    """N=8,388,608, D=32, K=4096, G=410 (held-out sample seed 9), 40
+    iterations, without a proposal (the seeded form is checked against this
+    one in test_gpu_mlp.py and test_gpu_proposal.py)."""
+    w = synth.proposal_family(9)
+    km = kp.KMeans(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.C0).cuda(), w.G)
+    sampled_run(kp, km, w.X.astype(np.float64), w.max_iter, w.tol, seed=5)
+    km.close()
+
+
+def test_batched_large_problems(kp):
+    """The batched form with problems at the large corner of its recipe
+    (N up to 200,000, D = 128, K up to 512) next to small ones: each problem's
+    final labels (sampled) and objective against the oracle, and against the
+    same problem fitted alone."""
+    shapes = [(200000, 128, 512), (150000, 64, 400), (120000, 32, 300), (2000, 8, 8), (60000, 128, 64),
+              (1000, 32, 500)]
+    ws = [synth.batched_problem(dict(seed=900 + i, N=n, D=d, K=k, G=max(1, k // 10)))
+          for i, (n, d, k) in enumerate(shapes)]
+    probs = [(torch.from_numpy(w.X).cuda(), torch.from_numpy(w.C0).cuda(), w.G) for w in ws]
+    b = kp.KMeansBatch(probs)
+    b.fit(25, 0.0)
+    rng = np.random.default_rng(7)
+    for i, ((X, C0, G), w) in enumerate(zip(probs, ws)):
+        N, D = w.X.shape
+        K = w.C0.shape[0]
+        lab = torch.empty(N, dtype=torch.int32, device="cuda")
+        C = torch.empty(K, D, device="cuda")
+        J, n_it = b.get(i, lab, C)
+        lab, C = lab.cpu().numpy(), C.cpu().numpy().astype(np.float64)
+        X64 = w.X.astype(np.float64)
+        idx = rng.choice(N, min(N, 1 << 14), replace=False)
+        ref, _, _, _ = oracle.lloyd_assign(X64[idx], C)
+        assert np.array_equal(lab[idx], ref), i
+        Jref = oracle.lloyd_objective(X64, lab, C)
+        assert abs(J - Jref) <= OBJECTIVE_RTOL * Jref + 1e-12, i
+        km = kp.KMeans(X, C0, G)
+        lab1 = torch.empty(N, dtype=torch.int32, device="cuda")
+        r = km.fit(25, 0.0, lab1)
+        km.close()
+        assert r.n_iter == n_it, (i, r.n_iter, n_it)
+        assert np.array_equal(lab1.cpu().numpy(), lab), i
+    b.close()
