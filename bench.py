@@ -52,6 +52,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the sub-records of the other workloads (high-dim 4M, batched 512, proposal 8M)")
+    ap.add_argument("--form-steps", type=int, default=2, help="timed steps of each sub-record")
+    ap.add_argument("--form-warmup", type=int, default=1, help="warm-up steps of each sub-record")
+    ap.add_argument("--energy-seconds", type=float, default=5.0,
+                    help="length of the fit loop over which the board's energy counter is read (0: skip)")
     ap.add_argument("--workload", default="aniso1m", choices=["aniso1m", "highdim4m", "batched", "gsweep", "proposal"],
                     help="aniso1m: the 1M-point anisotropic job (default line); highdim4m: 4M points, "
                          "D=128, K=1024, stored as bfloat16; batched: 512 independent problems of uneven "
@@ -114,7 +120,7 @@ class ClockSampler:
         # raw samples in a scratch file (KPYNQ_CLOCKS_DIR, else the system's
         # temporary directory); the JSON line carries their summary
         d = os.environ.get("KPYNQ_CLOCKS_DIR") or tempfile.gettempdir()
-        self.path = os.path.join(d, f"kpynq_clocks_{os.getpid()}.csv")
+        self.path = os.path.join(d, f"kpynq_clocks_{os.getpid()}_{id(self):x}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -164,6 +170,59 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
                 "reasons": sorted(reasons), "power_w_mean": statistics.mean(pw) if pw else None}
+
+
+def energy_mj(gpu_id: str | None) -> float | None:
+    """The board's cumulative energy counter (mJ since the driver loaded):
+    NVML's total-energy query (read-only), else nvidia-smi's."""
+    import ctypes
+    try:
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() == 0:
+            h = ctypes.c_void_p()
+            rc = (nv.nvmlDeviceGetHandleByUUID(gpu_id.encode(), ctypes.byref(h)) if gpu_id
+                  else nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)))
+            e = ctypes.c_ulonglong(0)
+            if rc == 0 and nv.nvmlDeviceGetTotalEnergyConsumption(h, ctypes.byref(e)) == 0 and e.value > 0:
+                return float(e.value)
+    except (OSError, AttributeError):
+        pass
+    cmd = ["nvidia-smi", "--query-gpu=total_energy_consumption", "--format=csv,noheader,nounits"]
+    if gpu_id:
+        cmd[1:1] = ["-i", gpu_id]
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=10).stdout.strip().splitlines()
+        return float(out[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
+
+
+def energy_loop(run_one, units_per_call: float, seconds: float, gpu_id: str | None) -> dict | None:
+    """points*iters per joule over a loop of calls lasting at least `seconds`,
+    from the difference of the cumulative energy counter across the loop."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = energy_mj(gpu_id)
+    if e0 is None:
+        return None
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        run_one()
+        calls += 1
+        if calls % 8 == 0:
+            torch.cuda.synchronize()
+            if time.perf_counter() - t0 >= seconds:
+                break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    e1 = energy_mj(gpu_id)
+    if e1 is None or e1 <= e0:
+        return None
+    joules = (e1 - e0) / 1e3
+    return {"value": units_per_call * calls / joules, "unit": "points*iters/J", "joules": joules,
+            "seconds": dt, "calls": calls, "mean_power_w": joules / dt,
+            "source": "NVML total energy consumption (cumulative board counter, read-only) across the loop"}
 
 
 def energy_of(value: float, clocks: dict) -> dict | None:
@@ -400,6 +459,45 @@ def breakdown_of(kinds, working):
     return out
 
 
+def roofline_of(w, kinds, working, pstats, breakdown, workload) -> dict:
+    """The dominant kernel's achieved fraction of its roofline: algorithmic
+    units per working launch over its CUDA-event time (the bound with the
+    larger fraction of its measured peak is reported, the other beside it)."""
+    hbm_peak, tc_peak, peak_src = measured_peaks()
+    dom = max(breakdown, key=lambda k: breakdown[k]["ms_total"])
+    t_l = kinds[dom][1]
+    n_l = working.get(dom, kinds[dom][0])
+    per_launch_s = t_l / n_l / 1e3
+    roofs = []
+    for bound, units_l in algorithmic(dom, w, pstats, n_l):
+        if bound == "alu":
+            achieved = units_l / per_launch_s / 1e12
+            roofs.append({"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
+                          "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS, "_units": units_l,
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz x 1.5 flop/issue "
+                                         "(FSUB+FFMA mix)"})
+        elif bound == "tensor":
+            achieved = units_l / per_launch_s / 1e12
+            roofs.append({"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": tc_peak,
+                          "unit": "TFLOP/s", "frac": achieved / tc_peak, "_units": units_l,
+                          "peak_source": f"{peak_src} bf16_tflops (burst)"})
+        else:
+            achieved = units_l / per_launch_s / 1e9
+            roofs.append({"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": achieved / hbm_peak, "_units": units_l, "peak_source": f"{peak_src} hbm_gbs"})
+    roof = max(roofs, key=lambda r: r["frac"])
+    units_l = roof.pop("_units")
+    others = sorted((r for r in roofs if r is not roof), key=lambda r: -r["frac"])
+    if others:
+        roof["other_bound"] = {"bound": others[0]["bound"], "frac": others[0]["frac"]}
+    roof["traffic"] = ncu_traffic(dom, workload)
+    roof["algorithmic_per_launch"] = units_l
+    roof["launch_us"] = per_launch_s * 1e6
+    roof["launches_averaged"] = n_l
+
+    return roof
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -459,6 +557,7 @@ def run_ours(args):
         times, iters, kern, stats = timed_steps(km, args.steps, args.warmup, "filtered")
         torch.cuda.synchronize()
         barrier(ws)
+    clocks = clk.summary()  # now: later samplers of this process reuse the file
     ms = statistics.mean(times)
     units = w.N * statistics.mean(iters)
     ms_max, units_all = aggregate(ms, units, ws, dev)
@@ -482,38 +581,8 @@ def run_ours(args):
 
     # --- profiled pass: CUDA events around every launch ---
     kinds, working, pstats = profiled_pass(kpynq, X, C0, w, lab, C, stream, flush, args.profile_steps)
-    hbm_peak, tc_peak, peak_src = measured_peaks()
     breakdown = breakdown_of(kinds, working)
-    dom = max(breakdown, key=lambda k: breakdown[k]["ms_total"])
-    t_l = kinds[dom][1]
-    n_l = working.get(dom, kinds[dom][0])
-    per_launch_s = t_l / n_l / 1e3
-    roofs = []
-    for bound, units_l in algorithmic(dom, w, pstats, n_l):
-        if bound == "alu":
-            achieved = units_l / per_launch_s / 1e12
-            roofs.append({"kernel": dom, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
-                          "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS, "_units": units_l,
-                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz x 1.5 flop/issue "
-                                         "(FSUB+FFMA mix)"})
-        elif bound == "tensor":
-            achieved = units_l / per_launch_s / 1e12
-            roofs.append({"kernel": dom, "bound": "tensor", "achieved": achieved, "peak": tc_peak,
-                          "unit": "TFLOP/s", "frac": achieved / tc_peak, "_units": units_l,
-                          "peak_source": f"{peak_src} bf16_tflops (burst)"})
-        else:
-            achieved = units_l / per_launch_s / 1e9
-            roofs.append({"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                          "frac": achieved / hbm_peak, "_units": units_l, "peak_source": f"{peak_src} hbm_gbs"})
-    roof = max(roofs, key=lambda r: r["frac"])
-    units_l = roof.pop("_units")
-    others = sorted((r for r in roofs if r is not roof), key=lambda r: -r["frac"])
-    if others:
-        roof["other_bound"] = {"bound": others[0]["bound"], "frac": others[0]["frac"]}
-    roof["traffic"] = ncu_traffic(dom, args.workload)
-    roof["algorithmic_per_launch"] = units_l
-    roof["launch_us"] = per_launch_s * 1e6
-    roof["launches_averaged"] = n_l
+    roof = roofline_of(w, kinds, working, pstats, breakdown, args.workload)
 
     # --- end to end through the C ABI with host buffers ---
     Xh = device_points(w, None, pinned=True)
@@ -532,6 +601,22 @@ def run_ours(args):
             et.append(time.perf_counter() - t0)
             ei.append(r.n_iter)
     e2e_value = w.N * statistics.mean(ei) / statistics.mean(et)
+    # energy: fits looped for at least --energy-seconds, cumulative board counter
+    energy = None
+    if args.energy_seconds > 0:
+        def one_fit():
+            km.reset(C0)
+            km.fit(w.max_iter, w.tol, lab, C, with_stats=False)
+        energy = energy_loop(one_fit, w.N * statistics.mean(iters), args.energy_seconds, gpu_uuid())
+    if energy is None:  # no energy counter: mean sampled power over the timed steps
+        energy = energy_of(value, clocks)
+    fstats = km.final_stats()
+    near = {"n_recheck_total": int(sum(s_["n_recheck"] for s_ in stats) + fstats["n_recheck"]),
+            "n_settle_total": int(sum(s_["n_settle"] for s_ in stats) + fstats["n_settle"]),
+            "per_iteration_n_recheck": [s_["n_recheck"] for s_ in stats],
+            "what": "n_recheck: points whose label was settled in FP64 (the FP32 error bound could not "
+                    "order their two nearest centroids); n_settle: rows the tensor-core pass sent to the "
+                    "exact settle.  Labels are exact for all of them."}
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + C0h.numel() * 4),
            "d2h_bytes_per_step": int(labh.numel() * 4 + Ch.numel() * 4 + 8 + 4),
@@ -544,6 +629,26 @@ def run_ours(args):
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, oracle_sample(w, ORACLE_WORK), 3)
+    forms = None
+    if not args.no_forms and args.workload == "aniso1m":
+        km.close()
+        del X
+        torch.cuda.empty_cache()
+        forms = {}
+        fs, fw = args.form_steps, args.form_warmup
+        for name, fn in (("highdim4m", lambda: highdim_record(args, dev, fs, fw)),
+                         ("batched512", lambda: batched_record(args, dev, steps=fs, warmup=fw)),
+                         ("proposal8m", lambda: proposal_record(args, dev, log=log, steps=fs, warmup=fw))):
+            t0 = time.perf_counter()
+            try:
+                rec = fn()
+                rec.pop("_units", None)
+                rec["wall_s"] = time.perf_counter() - t0
+            except Exception as e:  # one form failing must not lose the main line
+                rec = {"error": f"{type(e).__name__}: {e}"}
+            forms[name] = rec
+            torch.cuda.empty_cache()
+            log(f"[form {name}] {time.perf_counter() - t0:.1f} s")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -554,8 +659,9 @@ def run_ours(args):
                    "storage": w.meta.get("storage", "f32"),
                    "l2": f"flushed between steps (256 MiB write); X is {w.N * w.D * 4 >> 20} MiB > L2",
                    "parallelism": f"replicas x{ws}"},
-        "clocks": clk.summary(),
-        "energy": energy_of(value, clk.summary()),
+        "clocks": clocks,
+        "energy": energy,
+        "near_ties": near,
         "e2e": e2e,
         "gpu_launches": kern,
         "roofline": roof,
@@ -570,9 +676,11 @@ def run_ours(args):
         "vs_plain_lloyd_fp32": value / lloyd32_value,
         "paths": [s["path"] for s in stats],
         "kernel_breakdown": breakdown,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
-    km.close()
+    if forms is None:
+        km.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -582,53 +690,79 @@ def run_batched(args):
     """512 independent problems (N ~ logU[1e3, 2e5], D in {8,32,64,128},
     K ~ logU[8,512], G = K/10, 25 iterations each) fitted by one graph launch
     of the batched form, against the same problems fitted one after another
-    with single contexts.  Metric: points x iterations per second over the
-    batch."""
+    with single contexts, and against batched plain Lloyd.  Metric: points x
+    iterations per second over the batch."""
+    import torch
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    rec = batched_record(args, torch.device("cuda", local), seed0=1000 * rank)
+    units, ms = rec.pop("_units"), rec["ms_per_step"]
+    ms_max, units_all = aggregate(ms, units, ws_, torch.device("cuda", local))
+    if rank != 0:
+        return
+    line = {"metric": "points*iters/s (batched filtered K-means, 512 problems, exact labels)",
+            "value": units_all / (ms_max / 1e3), "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic"}
+    line.update(rec)
+    line["ms_per_step"] = ms_max
+    line["config"]["parallelism"] = f"replicas x{ws_}"
+    print(json.dumps(line), flush=True)
+
+
+def batched_record(args, dev, seed0=0, steps=None, warmup=None) -> dict:
     import tempfile
     import torch
     from paper_1905_09345_gb300 import kpynq, synth
-    ws_, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    specs = synth.batched_problems(args.problems, seed0=1000 * rank)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    t0 = time.perf_counter()
+    specs = synth.batched_problems(args.problems, seed0=seed0)
     works = [synth.batched_problem(s) for s in specs]
-    dev = torch.device("cuda", local)
+    gen_s = time.perf_counter() - t0
     probs = [(torch.from_numpy(w.X).to(dev), torch.from_numpy(w.C0).to(dev), w.G) for w in works]
     stream = torch.cuda.current_stream(dev)
     max_iter = works[0].max_iter
     cache = os.path.join(tempfile.gettempdir(), f"kpynq_tune_{os.getpid()}.txt")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed_batch(b):
+        def one_step():
+            flush.zero_()
+            b.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.fit(max_iter, 0.0)
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+        for _ in range(warmup):
+            one_step()
+        return [one_step() for _ in range(steps)]
+
     t0 = time.perf_counter()
     b = kpynq.KMeansBatch(probs, stream=stream, tune_cache=cache)
     init_s = time.perf_counter() - t0
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def one_step():
-        flush.zero_()
-        b.reset()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.fit(max_iter, 0.0)
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
-
-    for _ in range(args.warmup):
-        one_step()
     with ClockSampler(gpu_uuid()) as clk:
-        times = [one_step() for _ in range(args.steps)]
+        times = timed_batch(b)
     iters = [b.get(i)[1] for i in range(len(works))]
     units = sum(w.X.shape[0] * it for w, it in zip(works, iters))
     ms = statistics.mean(times)
-    ms_max, units_all = aggregate(ms, units, ws_, dev)
-    value = units_all / (ms_max / 1e3)
     switches = sorted(set(round(b.switch(i), 2) for i in range(len(works))))
     b.close()
+    # batched plain Lloyd: the same problems, every distance every iteration
+    bl = kpynq.KMeansBatch(probs, stream=stream, algo=kpynq.KM_ALGO_LLOYD)
+    ltimes = timed_batch(bl)
+    liters = [bl.get(i)[1] for i in range(len(works))]
+    lunits = sum(w.X.shape[0] * it for w, it in zip(works, liters))
+    bl.close()
     # the same problems, one fit after another (single contexts, graphs recorded beforehand)
     kms = [kpynq.KMeans(X, C0, G, stream=stream) for X, C0, G in probs]
-    for km, (X, C0, G) in zip(kms, probs):
+    for km in kms:
         km.fit(max_iter, 0.0, with_stats=False)
     seq = []
-    for _ in range(max(1, min(3, args.steps))):
+    for _ in range(max(1, min(3, steps))):
         for km, (X, C0, G) in zip(kms, probs):
             km.reset(C0)
         torch.cuda.synchronize()
@@ -639,28 +773,76 @@ def run_batched(args):
         seq.append(time.perf_counter() - t1)
     for km in kms:
         km.close()
-    seq_value = units / statistics.mean(seq)
     try:
         os.remove(cache)
     except OSError:
         pass
-    if rank != 0:
-        return
-    line = {
-        "metric": "points*iters/s (batched filtered K-means, 512 problems, exact labels)", "value": value,
-        "unit": UNIT, "n_gpus": ws_, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    value = units / (ms / 1e3)
+    lvalue = lunits / (statistics.mean(ltimes) / 1e3)
+    seq_value = units / statistics.mean(seq)
+    return {
+        "value": value, "ms_per_step": ms, "_units": units,
         "config": {"workload": f"batched{len(works)}", "problems": len(works),
                    "points": int(sum(w.X.shape[0] for w in works)), "max_iter": max_iter,
                    "step": "kmeans_batch_reset + kmeans_batch_fit (one graph launch)",
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws_}"},
-        "clocks": clk.summary(),
-        "energy": energy_of(value, clk.summary()),
-        "init_s": init_s, "tuned_switches": switches,
+                   "l2": "flushed between steps (256 MiB write)"},
+        "clocks": clk.summary(), "init_s": init_s, "generate_s": gen_s, "tuned_switches": switches,
+        "batched_plain_lloyd": {"value": lvalue, "ms_per_step": statistics.mean(ltimes)},
+        "vs_batched_plain_lloyd": value / lvalue,
         "sequential_single_contexts": {"value": seq_value, "s_per_step": statistics.mean(seq)},
         "vs_sequential": value / seq_value,
     }
-    print(json.dumps(line), flush=True)
+
+
+def highdim_record(args, dev, steps, warmup) -> dict:
+    """The high-dimension job (N=4,194,304, D=128, K=1024, G=103, bfloat16
+    storage, 30 iterations): the filtered method and plain Lloyd, both with
+    tensor-core dense passes, on the same GPU and inputs."""
+    import torch
+    from paper_1905_09345_gb300 import kpynq, synth
+    t0 = time.perf_counter()
+    w = synth.highdim_4m()
+    gen_s = time.perf_counter() - t0
+    X = device_points(w, dev)
+    C0 = torch.from_numpy(w.C0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    lab = torch.empty(w.N, dtype=torch.int32, device=dev)
+    C = torch.empty(w.K, w.D, dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    with ClockSampler(gpu_uuid()) as clk:
+        for name, algo in (("filtered", kpynq.KM_ALGO_FILTERED), ("plain_lloyd", kpynq.KM_ALGO_LLOYD)):
+            km = kpynq.KMeans(X, C0, w.G, stream=stream, algo=algo)
+            times, iters = [], []
+            for i in range(warmup + steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                km.reset(C0)
+                r = km.fit(w.max_iter, w.tol, lab, C, with_stats=False)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= warmup:
+                    times.append(e0.elapsed_time(e1))
+                    iters.append(r.n_iter)
+            st = km.stats(0, iters[-1]) + [km.final_stats()]
+            km.close()
+            ms = statistics.mean(times)
+            out[name] = {"value": w.N * statistics.mean(iters) / (ms / 1e3), "ms_per_fit": ms, "iters": iters[-1],
+                         "skip_fraction": 1.0 - sum(s_["n_dist"] for s_ in st[:-1]) / (w.N * w.K * (len(st) - 1)),
+                         "n_recheck_total": int(sum(s_["n_recheck"] for s_ in st)),
+                         "n_settle_total": int(sum(s_["n_settle"] for s_ in st)),
+                         "paths": [s_["path"] for s_ in st[:-1]]}
+    kinds, working, pstats = profiled_pass(kpynq, X, C0, w, lab, C, stream, flush, 1)
+    breakdown = breakdown_of(kinds, working)
+    return {"config": {"workload": w.name, "N": w.N, "D": w.D, "K": w.K, "G": w.G, "max_iter": w.max_iter,
+                       "storage": "bf16", "l2": "flushed between steps"},
+            "generate_s": gen_s, "clocks": clk.summary(),
+            "filtered": out["filtered"], "plain_lloyd": out["plain_lloyd"],
+            "plain_lloyd_dense": "BF16x3 tensor cores (tcgen05, streamed centroid blocks) + exact settle",
+            "vs_plain_lloyd": out["filtered"]["value"] / out["plain_lloyd"]["value"],
+            "roofline": roofline_of(w, kinds, working, pstats, breakdown, "highdim4m"),
+            "kernel_breakdown": breakdown}
 
 
 def run_gsweep(args):

@@ -658,6 +658,13 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     // default switch: the tensor-core dense pass costs about as much as the
     // survivor kernel with 70% of the points surviving; the FP32 one more
     p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.7f : 0.9f);
+    if (c->use_tc && !filtered && K > 256) {
+        // plain Lloyd with streamed centroid blocks: the pass still writes
+        // group bounds, so that the exact settle of a row visits only the
+        // groups that can hold its winner instead of all K centroids
+        INIT_CUDA(dalloc(c, &p.lb, (size_t)N * p.Gp));
+        INIT_CUDA(cudaMemsetAsync(p.lb, 0, (size_t)N * p.Gp * 4, s));
+    }
     if (c->use_tc) {  // the two bfloat16 halves of X, made once
         uint16_t *xh, *xl;
         const int Dt = tc_dim(D);  // zero-padded width of the operand copies

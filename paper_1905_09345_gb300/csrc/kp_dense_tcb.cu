@@ -248,7 +248,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float c2max = __fmul_ru(*c2max_s, 1.0f + 1.0f / 1024);
         const float cmax = sqrt_hi(c2max);
         const float ec2 = __fmul_ru(cfg.e_c2, c2max);
-        const bool bounds = p.algo == KM_ALGO_FILTERED;  // plain Lloyd keeps no bounds
+        // the filtered method keeps every bound; plain Lloyd keeps only the
+        // group bounds, for the exact settle's candidate groups
+        const bool bounds = p.algo == KM_ALGO_FILTERED;
+        const bool has_lb = p.lb != nullptr;
         const int wrow = (warp - 2) * 32;      // this warp's rows in the staging area
         float *row = stage + (size_t)(wrow + lane) * cfg.srow;
         const uint32_t row_addr = smem_u32(row);
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float *st0 = stage + (size_t)wrow * cfg.srow;
                 for (int e = lane; e < rows * cnt; e += 32) {
                     const int rw = e / cnt, s = e - rw * cnt;
-                    if (bounds && gfirst + s < G) p.lb[(n0 + rw) * p.Gp + gfirst + s] = st0[rw * cfg.srow + s];
+                    if (has_lb && gfirst + s < G) p.lb[(n0 + rw) * p.Gp + gfirst + s] = st0[rw * cfg.srow + s];
                 }
                 __syncwarp();
                 gfirst += cnt;
@@ -351,9 +354,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!need) p.label[n] = best;
                 // the winner's group excludes the winner: every other column is
                 // at least the runner-up; the smallest group bound is that bound
+                const float lw = b2 == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, b2), E));
+                if (has_lb) p.lb[n * p.Gp + group_of(bm, best)] = lw;
                 if (bounds) {
-                    const float lw = b2 == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xlo, b2), E));
-                    p.lb[n * p.Gp + group_of(bm, best)] = lw;
                     p.lbg[n] = lw;
                     p.u[n] = sqrt_hi(__fadd_ru(__fadd_ru(xup, b1), E));
                     p.stamp[n] = make_stamp(v, v);

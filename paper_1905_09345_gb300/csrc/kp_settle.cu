@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kSettleThreads, 1) k_settle(Params p, int firs
                 };
                 // the candidates in ascending index (a sub-warp-uniform walk)
                 auto for_groups = [&](auto &&fn) __attribute__((always_inline)) {
-                    if (q.gmask == ~0ull || (q.gmask == 0ull && !bounds)) {
+                    if (q.gmask == ~0ull || (q.gmask == 0ull && !p.lb)) {
                         fn(0, K);
                         return;
                     }
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle_t(Params p, int fi
     unsigned long long c_changed = 0, c_recheck = 0;
     // the candidates of a request: the centroids of the masked groups; all K
     // when the mask holds every group
-    auto all_of = [&](const SettleReq &q) { return q.gmask == ~0ull || (q.gmask == 0ull && !bounds); };
+    auto all_of = [&](const SettleReq &q) { return q.gmask == ~0ull || (q.gmask == 0ull && !p.lb); };
     // dynamic schedule: each warp takes the next 32 requests (one per lane)
     // from a counter; the requests differ in work, and a fixed split left
     // many SMs idle while a few finished their share
