@@ -276,6 +276,37 @@ KM_API int kmeans_lloyd_step_noalloc(const float *X, int64_t N, int32_t D, const
                                      int32_t K, int32_t *labels, float *C_new,
                                      double *objective, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Sharded iterations: one problem split by rows across processes (one per
+ * GPU).  Each process makes a context over its own rows with the same C^0,
+ * K, G and options.  An iteration is then
+ *   kmeans_shard_assign   this shard's assignment from C^t (the filters and
+ *                         the distance calculator of Sec. I, on its rows),
+ *                         and its cluster sums about C^t: S (K x D, FP64),
+ *                         Q (K, FP64: sum ||x - c_k^t||^2 over its points of
+ *                         cluster k), cnt (K) and its number of label changes;
+ *   (the caller sums S, Q, cnt and n_changed over the shards: one all-reduce)
+ *   kmeans_shard_update   the update from the summed statistics: C^{t+1},
+ *                         drift, J_t = sum_k Q_k and the stop rule, the same
+ *                         on every shard.
+ * The filters' bounds are per point, so they need no exchange; the drift is
+ * computed from the same sums on every shard.  stats->done (of the update)
+ * says the stop rule holds (no label changed, or a relative decrease of J
+ * below tol); the caller stops then, or after its own iteration budget, and
+ * makes a final assignment to the returned centroids: one more
+ * kmeans_shard_assign, the all-reduce, and kmeans_shard_update with
+ * final_pass = 1, which leaves the centroids as they are and writes J of
+ * that assignment to *objective.  Labels stay local (kmeans_get_labels).
+ * Arrays may be host or device memory.  Errors: KM_EINVAL, KM_ESTATE (an
+ * assignment without its update, or the reverse), the codes of
+ * kmeans_iterate.
+ * ------------------------------------------------------------------------ */
+KM_API int kmeans_shard_assign(kmeans_ctx *ctx, double tol, double *S, double *Q, int64_t *cnt,
+                               int64_t *n_changed);
+KM_API int kmeans_shard_update(kmeans_ctx *ctx, int32_t final_pass, const double *S, const double *Q,
+                               const int64_t *cnt, int64_t n_changed, kmeans_iter_stats *stats,
+                               double *objective);
+
 /* Free the context and everything it allocated.  NULL is a no-op. */
 KM_API void kmeans_destroy(kmeans_ctx *ctx);
 

@@ -6,7 +6,7 @@ seeded input generators.  Importing this package loads nothing; the binding
 loads the library on first use and raises if it is missing (there is no CPU
 fallback).
 """
-__all__ = ["synth", "kpynq"]
+__all__ = ["synth", "kpynq", "sharded"]
 
 
 def __getattr__(name):

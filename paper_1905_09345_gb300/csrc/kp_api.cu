@@ -51,6 +51,11 @@ struct kmeans_ctx {
     float *cc_table = nullptr;
     int32_t *pred = nullptr;
     bool have_final = false;  // a fit finished: its final-assignment record is kept
+    // sharded iterations (kmeans_shard_*): the cluster sums of every
+    // assignment are rebuilt from this shard's points about the current
+    // centroids, so that every shard's sums share one reference point
+    bool shard = false;
+    bool shard_pending = false;  // an assignment waits for its update
     int t_host = 0;        // iterations run (mirrors ctrl->t after each call)
     int v_host = 0;        // table version (mirrors ctrl->v)
     bool broken = false;
@@ -301,7 +306,7 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
             e = timed(c, s, KM_KERNEL_SETTLE, [&] { return launch_settle(p, s, first, respect_done, n); });
             if (e != cudaSuccess) return e;
         }
-        return enqueue_stats(c, p, s, first ? 1 : 0, respect_done);
+        return enqueue_stats(c, p, s, (first || c->shard) ? 1 : 0, respect_done);
     }
     // filtered: global filter, then either the survivor kernel or -- when the
     // filter kernel finds too many survivors -- the dense pass (each of the
@@ -321,7 +326,7 @@ cudaError_t enqueue_assign(kmeans_ctx *c, const Params &p, cudaStream_t s, bool 
     }
     // both the survivor kernel and the dense pass append to the moved-point list
     // (a seeded iteration 0 recomputes every cluster sum)
-    return enqueue_stats(c, p, s, first ? 1 : 0, respect_done);
+    return enqueue_stats(c, p, s, (first || c->shard) ? 1 : 0, respect_done);
 }
 
 cudaError_t enqueue_update(kmeans_ctx *c, const Params &p, cudaStream_t s, int final_only, int respect_done) {
@@ -729,6 +734,60 @@ KM_API int kmeans_iterate(kmeans_ctx *c, kmeans_iter_stats *stats) {
     return KM_OK;
 }
 
+KM_API int kmeans_shard_assign(kmeans_ctx *c, double tol, double *S, double *Q, int64_t *cnt,
+                               int64_t *n_changed) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!S || !Q || !cnt || !n_changed) return set_err(c, KM_EINVAL, "a pointer argument is NULL");
+    if (!(tol >= 0.0)) return set_err(c, KM_EINVAL, "tol must be >= 0");
+    if (c->shard_pending) return set_err(c, KM_ESTATE, "the previous shard assignment has not been updated");
+    if (c->proposal) return set_err(c, KM_EINVAL, "sharded iterations do not take a learned proposal");
+    DeviceGuard dg(c->dev);
+    if ((rc = ensure_tables(c, 2))) return rc;
+    Params &p = c->p;
+    p.tcap = c->tcap;
+    cudaStream_t s = c->stream;
+    c->shard = true;
+    // a stop rule without an iteration budget: the caller stops on stats.done
+    KP_CUDA(c, timed(c, s, KM_KERNEL_OTHER, [&] { return launch_arm(p, s, 1 << 30, tol); }));
+    const bool first = c->t_host == 0;
+    KP_CUDA(c, enqueue_assign(c, p, s, first || p.algo == KM_ALGO_LLOYD, first, 0));
+    if ((rc = sync_and_check(c))) return rc;
+    KP_CUDA(c, cudaMemcpyAsync(S, p.S, (size_t)p.K * p.D * 8, cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaMemcpyAsync(Q, p.Q, (size_t)p.K * 8, cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaMemcpyAsync(cnt, p.cnt, (size_t)p.K * 8, cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaStreamSynchronize(s));
+    *n_changed = (int64_t)c->ctrl_host->n_changed;
+    c->shard_pending = true;
+    return KM_OK;
+}
+
+KM_API int kmeans_shard_update(kmeans_ctx *c, int32_t final_pass, const double *S, const double *Q,
+                               const int64_t *cnt, int64_t n_changed, kmeans_iter_stats *stats, double *objective) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!S || !Q || !cnt) return set_err(c, KM_EINVAL, "a pointer argument is NULL");
+    if (!c->shard_pending) return set_err(c, KM_ESTATE, "no shard assignment is waiting for its update");
+    if (n_changed < 0) return set_err(c, KM_EINVAL, "n_changed must be >= 0");
+    DeviceGuard dg(c->dev);
+    Params &p = c->p;
+    cudaStream_t s = c->stream;
+    KP_CUDA(c, cudaMemcpyAsync(p.S, S, (size_t)p.K * p.D * 8, cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaMemcpyAsync(p.Q, Q, (size_t)p.K * 8, cudaMemcpyDefault, s));
+    KP_CUDA(c, cudaMemcpyAsync(p.cnt, cnt, (size_t)p.K * 8, cudaMemcpyDefault, s));
+    const unsigned long long nc = (unsigned long long)n_changed;
+    KP_CUDA(c, cudaMemcpyAsync(&p.ctrl->n_changed, &nc, 8, cudaMemcpyHostToDevice, s));
+    c->shard_pending = false;
+    const int t = c->t_host;
+    KP_CUDA(c, enqueue_update(c, p, s, final_pass ? 1 : 0, 0));
+    if ((rc = sync_and_check(c))) return rc;
+    const int slot = final_pass ? kStatsCap : (t % kStatsCap);
+    if (stats) KP_CUDA(c, cudaMemcpy(stats, p.stats + slot, sizeof(*stats), cudaMemcpyDeviceToHost));
+    if (final_pass && objective) KP_CUDA(c, cudaMemcpy(objective, &p.ctrl->jfinal, 8, cudaMemcpyDefault));
+    if (final_pass) c->have_final = true;
+    return KM_OK;
+}
+
 KM_API int kmeans_fit(kmeans_ctx *c, int32_t max_iter, double tol, int32_t *labels, float *centroids,
                       double *objective, int32_t *n_iter) {
     int rc = check_ctx(c);
@@ -857,6 +916,7 @@ KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
     KP_CUDA(c, cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)p.D * 4, (size_t)p.D * 4, p.K,
                                  cudaMemcpyDefault, s));
     KP_CUDA(c, cudaMemcpyAsync(p.R, p.C, (size_t)p.K * p.Dp * 4, cudaMemcpyDeviceToDevice, s));
+    c->shard_pending = false;
     KP_CUDA(c, cudaMemsetAsync(p.S, 0, (size_t)p.K * p.D * 8, s));
     KP_CUDA(c, cudaMemsetAsync(p.Q, 0, (size_t)p.K * 8, s));
     KP_CUDA(c, cudaMemsetAsync(p.cnt, 0, (size_t)p.K * 8, s));

@@ -122,6 +122,11 @@ def lib():
         L.kmeans_batch_destroy.restype = None
         L.kmeans_batch_last_error.argtypes = [vp]
         L.kmeans_batch_last_error.restype = ctypes.c_char_p
+        L.kmeans_shard_assign.argtypes = [vp, dbl, vp, vp, vp, ctypes.POINTER(i64)]
+        L.kmeans_shard_assign.restype = ctypes.c_int
+        L.kmeans_shard_update.argtypes = [vp, i32, vp, vp, vp, i64, ctypes.POINTER(kmeans_iter_stats),
+                                          ctypes.POINTER(dbl)]
+        L.kmeans_shard_update.restype = ctypes.c_int
         u64, f32 = ctypes.c_uint64, ctypes.c_float
         L.kmeans_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, u64, vp]
         L.kmeans_mlp_create.restype = ctypes.c_int
@@ -313,6 +318,22 @@ def kmeans_lloyd_step_noalloc(X, N: int, D: int, C, K: int, labels, C_new, objec
     st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().kmeans_lloyd_step_noalloc(_addr(X), N, D, _addr(C), K, _addr(labels), _addr(C_new),
                                            _addr(objective), st), None)
+
+
+def kmeans_shard_assign(ctx, tol: float, S, Q, cnt) -> int:
+    """This shard's assignment and cluster sums (into S, Q, cnt); returns its label changes."""
+    nc = ctypes.c_int64()
+    _check(lib().kmeans_shard_assign(ctx, tol, _addr(S), _addr(Q), _addr(cnt), ctypes.byref(nc)), ctx)
+    return nc.value
+
+
+def kmeans_shard_update(ctx, final_pass: bool, S, Q, cnt, n_changed: int):
+    """The update from the summed statistics; returns (stats dict, objective of a final pass)."""
+    st = kmeans_iter_stats()
+    J = ctypes.c_double(float("nan"))
+    _check(lib().kmeans_shard_update(ctx, int(final_pass), _addr(S), _addr(Q), _addr(cnt), n_changed,
+                                     ctypes.byref(st), ctypes.byref(J)), ctx)
+    return st.as_dict(), J.value
 
 
 def kmeans_destroy(ctx) -> None:
