@@ -15,6 +15,10 @@ Two independent C implementations, each written from its definition:
   filter, point-level filter, distance calculator, bound refresh; Sec. I), in
   FP64, with per-iteration skip counters.
 
+* ``kmeanspp.c`` (O4): k-means++ seeding (D^2 sampling) with the random
+  numbers as inputs and an exactly reproducible draw -- an initialisation the
+  library offers beside the caller's centroids (the paper takes them as given).
+
 * ``mlp.py`` (O3): the learned group proposal's MLP (GELU layers, softmax
   cross-entropy, Adam) in numpy FP64 -- a layered form of the library, not in
   the paper; the filtered method's labels do not depend on it.
@@ -44,7 +48,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
-_SOURCES = {"lloyd": "lloyd.c", "ti": "ti_lloyd.c"}
+_SOURCES = {"lloyd": "lloyd.c", "ti": "ti_lloyd.c", "pp": "kmeanspp.c"}
 _lock = threading.Lock()
 _libs: dict = {}
 
@@ -136,6 +140,9 @@ def _declare(lib, name: str) -> None:
         lib.o1_fit.restype = _i32
         lib.o1_fit.argtypes = [_dp, _i64, _i32, _dp, _i32, _i32, _f64, _ip, _dp,
                                _vp, _vp, _vp]
+    elif name == "pp":
+        lib.o4_kmeanspp.restype = _i32
+        lib.o4_kmeanspp.argtypes = [_dp, _i64, _i32, _i32, _dp, _lp, _vp]
     else:
         lib.o2_init_assign.restype = None
         lib.o2_init_assign.argtypes = [_dp, _i64, _i32, _dp, _i32, _i32, _ip, _ip,
@@ -322,6 +329,26 @@ def ti_fit(X, C0, G: int, max_iter: int, tol: float = 0.0, grp=None, *,
     if keep_history:
         out["labels_hist"] = lh[:n_iter].copy()
     return out
+
+
+# ----------------------------------------------------------------------------
+# O4: k-means++ seeding
+# ----------------------------------------------------------------------------
+def kmeanspp(X, K: int, u, *, lib=None):
+    """k-means++ centre indices (O4, ``kmeanspp.c``): ``u`` holds K uniforms
+    in [0, 1), one per centre.  Returns ``(idx int64 (K,), dmin (N,))``, dmin
+    the final squared distance of every point to its nearest chosen centre."""
+    lib = _load("pp", lib)
+    X = _as64(X)
+    N, D = X.shape
+    u = _as64(u)
+    if u.shape != (K,):
+        raise ValueError("u must hold K uniforms")
+    idx = np.empty(K, np.int64)
+    dmin = np.empty(N, np.float64)
+    if lib.o4_kmeanspp(X, N, D, K, u, idx, _ptr(dmin)) != 0:
+        raise ValueError("bad arguments or allocation failure")
+    return idx, dmin
 
 
 # ----------------------------------------------------------------------------
