@@ -307,6 +307,27 @@ KM_API int kmeans_shard_update(kmeans_ctx *ctx, int32_t final_pass, const double
                                const int64_t *cnt, int64_t n_changed, kmeans_iter_stats *stats,
                                double *objective);
 
+/*
+ * k-means++ seeding (an initialisation beside the caller's centroids; the
+ * paper takes them as given): the first centre is the point floor(u[0] * N),
+ * each further centre j a point drawn with probability proportional to
+ * D(x)^2, its squared distance to the nearest centre chosen so far
+ * (Arthur and Vassilvitskii, SODA 2007), using the uniform u[j] in [0, 1).
+ * The draw is exact: D(x)^2 in FP64 (sum over i ascending, no fused
+ * multiply-add), weights floor(D(x)^2 * 2^s) as 64-bit integers with 2^s the
+ * power of two that puts the largest in [2^31, 2^32), T = floor(u[j] * W)
+ * for their sum W, and the centre is the first point whose running weight
+ * sum exceeds T (uniform floor(u[j] * N) when W = 0) -- so the same uniforms
+ * give the same centres on any implementation.  X: N x D float32, device
+ * memory; u: K doubles; centroids: K x D float32 out; indices: K int64 out
+ * (nullable); u and the outputs may be host or device memory.  Work on
+ * `stream` with stream-ordered scratch (N + N / 1024 doubles); returns after
+ * it finished.  Errors: KM_EINVAL, KM_ENOMEM, KM_ECUDA; message in
+ * kmeans_last_error(NULL).
+ */
+KM_API int kmeans_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t K, const double *u,
+                                float *centroids, int64_t *indices, void *stream);
+
 /* Free the context and everything it allocated.  NULL is a no-op. */
 KM_API void kmeans_destroy(kmeans_ctx *ctx);
 

@@ -372,6 +372,13 @@ cudaError_t launch_arm(const Params &p, cudaStream_t s, int max_iter, double tol
 cudaError_t launch_set_cond(const Params &p, cudaStream_t s);
 cudaError_t launch_rebase(const Params &p, cudaStream_t s, int num_sms);
 cudaError_t launch_bounds_out(const Params &p, cudaStream_t s, float *u, float *lbg, float *lb, int num_sms);
+// k-means++ seeding (kp_kmeanspp.cu): K centres of X into C / idx; dmin (N
+// doubles), bsum (ceil(N / 1024)) and state (kmeanspp_state_bytes()) are
+// scratch; *err_out (host) is set nonzero if a drawn index fell out of range
+cudaError_t launch_kmeanspp(const float *X, int64_t N, int D, int K, const double *u, float *C, long long *idx,
+                            double *dmin, unsigned long long *bsum, void *state, cudaStream_t s, int num_sms,
+                            long long *err_out);
+size_t kmeanspp_state_bytes();
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t s, int num_sms);
 cudaError_t launch_bf16_to_f32(const uint16_t *in, int64_t n, float *out, cudaStream_t s, int num_sms);
 

@@ -127,6 +127,8 @@ def lib():
         L.kmeans_shard_update.argtypes = [vp, i32, vp, vp, vp, i64, ctypes.POINTER(kmeans_iter_stats),
                                           ctypes.POINTER(dbl)]
         L.kmeans_shard_update.restype = ctypes.c_int
+        L.kmeans_init_kmeanspp.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp]
+        L.kmeans_init_kmeanspp.restype = ctypes.c_int
         u64, f32 = ctypes.c_uint64, ctypes.c_float
         L.kmeans_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, u64, vp]
         L.kmeans_mlp_create.restype = ctypes.c_int
@@ -334,6 +336,12 @@ def kmeans_shard_update(ctx, final_pass: bool, S, Q, cnt, n_changed: int):
     _check(lib().kmeans_shard_update(ctx, int(final_pass), _addr(S), _addr(Q), _addr(cnt), n_changed,
                                      ctypes.byref(st), ctypes.byref(J)), ctx)
     return st.as_dict(), J.value
+
+
+def kmeans_init_kmeanspp(X, N: int, D: int, K: int, u, centroids, indices=None, stream=None) -> None:
+    """k-means++ seeding: K centres of X (device) from the K uniforms u."""
+    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().kmeans_init_kmeanspp(_addr(X), N, D, K, _addr(u), _addr(centroids), _addr(indices), st), None)
 
 
 def kmeans_destroy(ctx) -> None:
