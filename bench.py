@@ -638,7 +638,8 @@ def run_ours(args):
         fs, fw = args.form_steps, args.form_warmup
         for name, fn in (("highdim4m", lambda: highdim_record(args, dev, fs, fw)),
                          ("batched512", lambda: batched_record(args, dev, steps=fs, warmup=fw)),
-                         ("proposal8m", lambda: proposal_record(args, dev, log=log, steps=fs, warmup=fw))):
+                         ("proposal8m", lambda: proposal_record(args, dev, log=log, steps=fs, warmup=fw)),
+                         ("skewed1m", lambda: skewed_record(args, dev, fs, fw))):
             t0 = time.perf_counter()
             try:
                 rec = fn()
@@ -792,6 +793,56 @@ def batched_record(args, dev, seed0=0, steps=None, warmup=None) -> dict:
         "sequential_single_contexts": {"value": seq_value, "s_per_step": statistics.mean(seq)},
         "vs_sequential": value / seq_value,
     }
+
+
+def skewed_record(args, dev, steps, warmup) -> dict:
+    """The real-data-like skewed job (N=1,048,576, D=32, K=128, G=13) seeded by
+    k-means++ on the GPU: the seeding's time, then the filtered method and
+    plain Lloyd on the same GPU and inputs."""
+    import torch
+    from paper_1905_09345_gb300 import kpynq, synth
+    w = synth.skewed_mixture()
+    X = torch.from_numpy(w.X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    C0 = torch.empty(w.K, w.D, dtype=torch.float32, device=dev)
+    times = []
+    for i in range(warmup + steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kpynq.kmeans_init_kmeanspp(X, w.N, w.D, w.K, w.meta["pp_u"], C0, None, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            times.append(e0.elapsed_time(e1))
+    lab = torch.empty(w.N, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name, algo in (("filtered", kpynq.KM_ALGO_FILTERED), ("plain_lloyd", kpynq.KM_ALGO_LLOYD)):
+        km = kpynq.KMeans(X, C0, w.G, stream=stream, algo=algo)
+        ft, fi = [], []
+        for i in range(warmup + steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            km.reset(C0)
+            r = km.fit(w.max_iter, w.tol, lab, with_stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                ft.append(e0.elapsed_time(e1))
+                fi.append(r.n_iter)
+        st = km.stats(0, fi[-1])
+        km.close()
+        ms = statistics.mean(ft)
+        out[name] = {"value": w.N * statistics.mean(fi) / (ms / 1e3), "ms_per_fit": ms, "iters": fi[-1],
+                     "skip_fraction": 1.0 - sum(s_["n_dist"] for s_ in st) / (w.N * w.K * len(st)),
+                     "n_recheck_total": int(sum(s_["n_recheck"] for s_ in st)),
+                     "paths": [s_["path"] for s_ in st]}
+    return {"config": {"workload": w.name, "N": w.N, "D": w.D, "K": w.K, "G": w.G, "max_iter": w.max_iter,
+                       "tol": w.tol, "init": "k-means++ on the GPU (kmeans_init_kmeanspp)"},
+            "kmeanspp_ms": statistics.mean(times),
+            "filtered": out["filtered"], "plain_lloyd": out["plain_lloyd"],
+            "vs_plain_lloyd": out["filtered"]["value"] / out["plain_lloyd"]["value"]}
 
 
 def highdim_record(args, dev, steps, warmup) -> dict:

@@ -670,6 +670,29 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         INIT_CUDA(dalloc(c, &p.lb, (size_t)N * p.Gp));
         INIT_CUDA(cudaMemsetAsync(p.lb, 0, (size_t)N * p.Gp * 4, s));
     }
+    if (c->use_tc) {
+        // the tensor-core passes work on x - mu and c - mu, mu the mean of the
+        // initial centroids: distances do not change, but the error window of
+        // the bfloat16 products scales with ||x - mu|| ||c - mu|| instead of
+        // ||x|| ||c||, which matters for data far from the origin
+        std::vector<float> hc((size_t)K * D);
+        INIT_CUDA(cudaMemcpyAsync(hc.data(), init_centroids, hc.size() * 4, cudaMemcpyDefault, s));
+        INIT_CUDA(cudaStreamSynchronize(s));
+        std::vector<float> hm((size_t)p.Dp, 0.f);
+        for (int d = 0; d < D; ++d) {
+            double m = 0.0;
+            for (int k = 0; k < K; ++k) m += hc[(size_t)k * D + d];
+            hm[d] = (float)(m / K);
+        }
+        float *mu;
+        INIT_CUDA(dalloc(c, &mu, (size_t)p.Dp));
+        INIT_CUDA(cudaMemcpyAsync(mu, hm.data(), (size_t)p.Dp * 4, cudaMemcpyHostToDevice, s));
+        INIT_CUDA(cudaStreamSynchronize(s));  // hm is a host temporary
+        p.mu = mu;
+        // x - mu and c - mu are each rounded once (relative 2^-24 per coordinate):
+        // |s' - s| <= 2 u (1 + u) R^2 + 3 (u (1 + u) R)^2 for R = ||x - mu|| + ||c - mu||
+        p.e_cen = (float)(std::ldexp(1.0, -23) * 1.01);
+    }
     if (c->use_tc) {  // the two bfloat16 halves of X, made once
         uint16_t *xh, *xl;
         const int Dt = tc_dim(D);  // zero-padded width of the operand copies
@@ -677,7 +700,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         INIT_CUDA(dalloc(c, &xl, (size_t)N * Dt));
         // from the host copy when X is still there (the FP32 copy is made in the same pass)
         INIT_CUDA(launch_split_x(x_host_dev ? x_host_dev : p.X, N, D, Dt, xh, xl, s, c->num_sms,
-                                 x_host_dev ? c->X_own : nullptr));
+                                 x_host_dev ? c->X_own : nullptr, p.mu));
         x_host_dev = nullptr;
         p.Xh = xh;
         p.Xl = xl;

@@ -98,6 +98,10 @@ struct Params {
     uint32_t *stamp;     // N: (version of u) << 16 | (version of lbg, lb)
 
     float *C;            // K x Dp (padding columns are zero)
+    const float *mu;     // Dp: centre subtracted from points and centroids before the
+                         // tensor-core products (distances do not depend on it); NULL: none
+    float e_cen;         // the rounding of x - mu and c - mu moves a squared distance by
+                         // at most e_cen (||x - mu|| + max ||c - mu||)^2 (0 without mu)
     double *S;           // K x D   cluster sums (FP64)
     double *Q;           // K       sum of ||x - R_k||^2 per cluster (FP64)
     float *R;            // K x Dp  reference point of each cluster's Q (a copy of C made
@@ -353,7 +357,7 @@ int dense_tcb_kp(const Params &p);  // padded K of the split centroid copy
 cudaError_t launch_dense_tcb(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                              size_t smem_limit, int if_dense);
 cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
-                           int num_sms, float *Xcopy = nullptr);
+                           int num_sms, float *Xcopy = nullptr, const float *mu = nullptr);
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);

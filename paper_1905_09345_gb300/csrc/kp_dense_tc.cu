@@ -136,6 +136,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float4 b = *reinterpret_cast<const float4 *>(p.C + (size_t)row * p.Dp + q * 8 + 4);
             vals[0] = a.x; vals[1] = a.y; vals[2] = a.z; vals[3] = a.w;
             vals[4] = b.x; vals[5] = b.y; vals[6] = b.z; vals[7] = b.w;
+            if (p.mu)  // c - mu (mu's padding columns are zero)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) vals[i] = __fsub_rn(vals[i], p.mu[q * 8 + i]);
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) vals[i] = 0.f;
@@ -152,9 +155,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (k < K) {
                 const float *c = p.C + (size_t)k * p.Dp;
                 float a0 = 0.f, a1 = 0.f;
-                for (int d = 0; d + 1 < p.D; d += 2) {
-                    a0 = fmaf(c[d], c[d], a0);
-                    a1 = fmaf(c[d + 1], c[d + 1], a1);
+                for (int d = 0; d + 1 < p.D; d += 2) {  // ||c - mu||^2, the values split above
+                    const float v0 = p.mu ? __fsub_rn(c[d], p.mu[d]) : c[d];
+                    const float v1 = p.mu ? __fsub_rn(c[d + 1], p.mu[d + 1]) : c[d + 1];
+                    a0 = fmaf(v0, v0, a0);
+                    a1 = fmaf(v1, v1, a1);
                 }
                 s2 = a0 + a1;
                 cm = fmaxf(cm, s2);
@@ -296,6 +301,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 xlo = __fmul_rd(xn, cfg.xn_lo);
                 xup = __fmul_ru(xn, cfg.xn_hi);
                 E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
+                const float R = __fadd_ru(sqrt_hi(xup), cmax);  // bounds ||x - mu|| + ||c - mu||
+                E = __fmaf_ru(p.e_cen, __fmul_ru(R, R), E);
             }
             const uint32_t tb = tmem + (uint32_t)(grp_id * cfg.buf_cols) + ((uint32_t)(q * 32) << 16);
 
@@ -490,7 +497,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // X -> (x_h, x_l) bfloat16 copies with rows of Dt >= D coordinates (zero
 // padding), four elements per thread
-__global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, uint2 *Xl, float4 *Xcopy) {
+__global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, uint2 *Xl, float4 *Xcopy,
+                          const float *mu) {
     const int q4n = Dt / 4;
     const int64_t n4 = N * q4n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -498,7 +506,9 @@ __global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, u
         const int q4 = (int)(i - row * q4n);
         const float4 a = q4 * 4 < D ? *reinterpret_cast<const float4 *>(X + row * D + q4 * 4) : make_float4(0, 0, 0, 0);
         if (Xcopy && q4 * 4 < D) Xcopy[(row * D + q4 * 4) / 4] = a;  // the device copy, in the same pass
-        const float vv[4] = {a.x, a.y, a.z, a.w};
+        // x - mu, rounded once to FP32 (the padding stays exactly zero)
+        const float4 m = (mu && q4 * 4 < D) ? *reinterpret_cast<const float4 *>(mu + q4 * 4) : make_float4(0, 0, 0, 0);
+        const float vv[4] = {__fsub_rn(a.x, m.x), __fsub_rn(a.y, m.y), __fsub_rn(a.z, m.z), __fsub_rn(a.w, m.w)};
         uint32_t hw[2], lw[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -597,13 +607,13 @@ bool dense_tc_eligible(const Params &p, size_t smem_limit) {
 }
 
 cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
-                           int num_sms, float *Xcopy) {
+                           int num_sms, float *Xcopy, const float *mu) {
     const int64_t n4 = N * Dt / 4;  // D and Dt are multiples of 4
     const int64_t grid = std::min<int64_t>((n4 + 255) / 256, (int64_t)num_sms * 16);
     count_launch();
     k_split_x<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(X, N, D, Dt, reinterpret_cast<uint2 *>(Xh),
                                                                     reinterpret_cast<uint2 *>(Xl),
-                                                                    reinterpret_cast<float4 *>(Xcopy));
+                                                                    reinterpret_cast<float4 *>(Xcopy), mu);
     return cudaGetLastError();
 }
 

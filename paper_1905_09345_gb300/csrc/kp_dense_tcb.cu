@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) bar_arrive(&empty_a[g]);
             const float xlo = __fmul_rd(xn, cfg.xn_lo), xup = __fmul_ru(xn, cfg.xn_hi);
-            const float E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
+            const float R = __fadd_ru(sqrt_hi(xup), cmax);  // bounds ||x - mu|| + ||c - mu||
+            const float E = __fmaf_ru(p.e_cen, __fmul_ru(R, R), __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2));
             const float twoE = __fmul_ru(2.f, E);
             const int64_t n0 = (int64_t)tile * kTM + q * 32;
             const int rows = (int)max((int64_t)0, min((int64_t)32, p.N - n0));
@@ -407,7 +408,8 @@ __global__ void k_split_c(Params p, int Kp, int respect_done, int if_dense) {
     const int64_t total = (int64_t)Kp * Dt;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(i / Dt), d = (int)(i - (int64_t)k * Dt);
-        const float x = (k < p.K && d < D) ? p.C[(size_t)k * p.Dp + d] : 0.f;  // zero padding
+        float x = (k < p.K && d < D) ? p.C[(size_t)k * p.Dp + d] : 0.f;  // zero padding
+        if (p.mu && k < p.K && d < D) x = __fsub_rn(x, p.mu[d]);  // c - mu
         const __nv_bfloat16 h = __float2bfloat16_rn(x);
         const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
         p.Ch[i] = __bfloat16_as_ushort(h);
@@ -422,9 +424,11 @@ __global__ void k_split_c(Params p, int Kp, int respect_done, int if_dense) {
         if (lane == 0) {
             const float *c = p.C + (size_t)k * p.Dp;
             float a0 = 0.f, a1 = 0.f;
-            for (int d = 0; d + 1 < D; d += 2) {
-                a0 = fmaf(c[d], c[d], a0);
-                a1 = fmaf(c[d + 1], c[d + 1], a1);
+            for (int d = 0; d + 1 < D; d += 2) {  // ||c - mu||^2, the values split above
+                const float v0 = p.mu ? __fsub_rn(c[d], p.mu[d]) : c[d];
+                const float v1 = p.mu ? __fsub_rn(c[d + 1], p.mu[d + 1]) : c[d + 1];
+                a0 = fmaf(v0, v0, a0);
+                a1 = fmaf(v1, v1, a1);
             }
             p.cnorm[k] = a0 + a1;
         }

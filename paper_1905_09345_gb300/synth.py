@@ -171,6 +171,50 @@ def proposal_family(sample_seed: int, N: int = 1 << 23, D: int = 32, K: int = 40
                     dict(family_seed=family_seed, sample_seed=sample_seed))
 
 
+def skewed_mixture(N: int = 1 << 20, D: int = 32, K: int = 128, G: int = 13, seed: int = 6) -> Workload:
+    """Real-data-like skew (the paper's datasets are raw UCI tables of "a wide
+    range of size and dimensionality", Sec. II): K anisotropic blobs with
+    power-law sizes (weights proportional to rank^-1.2), features on scales
+    spread over three orders of magnitude (per-feature scale lognormal(0,
+    1.5)) around per-feature offsets up to 1000 scales, one feature in eight
+    rounded to integers (count-like attributes), 1% uniform outliers over the
+    bounding box and 2% exact duplicates of other rows.  Initial centroids:
+    k-means++ with the uniforms ``meta["pp_u"]`` (drawn after the data); C0
+    holds the first K rows until they are computed.  30 iterations or tol 1e-4."""
+    rng = np.random.default_rng(seed)
+    fscale = rng.lognormal(0.0, 1.5, size=D).astype(np.float32)
+    offset = (rng.uniform(0.0, 1000.0, size=D) * fscale).astype(np.float32)
+    centres = rng.uniform(-20.0, 20.0, size=(K, D)).astype(np.float32)
+    sig = rng.uniform(0.2, 2.0, size=(K, D)).astype(np.float32)
+    w = np.arange(1, K + 1, dtype=np.float64) ** -1.2
+    counts = rng.multinomial(N, w / w.sum())
+    blob = np.repeat(np.arange(K, dtype=np.int32), counts)
+    X = np.empty((N, D), np.float32)
+    chunk = 1 << 20
+    for a in range(0, N, chunk):
+        b = min(N, a + chunk)
+        bb = blob[a:b]
+        X[a:b] = centres[bb] + rng.standard_normal((b - a, D), dtype=np.float32) * sig[bb]
+    n_out = N // 100
+    lo, hi = X.min(axis=0), X.max(axis=0)
+    out_rows = rng.choice(N, n_out, replace=False)
+    X[out_rows] = rng.uniform(lo, hi, size=(n_out, D)).astype(np.float32)
+    blob[out_rows] = -1
+    X = X * fscale + offset
+    ints = np.arange(D) % 8 == 7
+    X[:, ints] = np.round(X[:, ints])
+    n_dup = N // 50
+    dst = rng.choice(N, n_dup, replace=False)
+    src = rng.choice(N, n_dup, replace=True)
+    X[dst] = X[src]
+    blob[dst] = blob[src]
+    perm = rng.permutation(N)
+    X = np.ascontiguousarray(X[perm])
+    u = rng.uniform(size=K)
+    return Workload(f"skewed_n{N}_d{D}_k{K}_g{G}", X, np.ascontiguousarray(X[:K]), G, 30, 1e-4, blob[perm],
+                    dict(seed=seed, pp_u=u, init="kmeans++"))
+
+
 def batched_problems(n_problems: int = 512, seed0: int = 0, n_lo: int = 1000, n_hi: int = 200000,
                      k_lo: int = 8, k_hi: int = 512):
     """Parameters of the batched workload: per problem p (seed0 + p),

@@ -135,3 +135,22 @@ def test_batched_large_problems(kp):
         assert r.n_iter == n_it, (i, r.n_iter, n_it)
         assert np.array_equal(lab1.cpu().numpy(), lab), i
     b.close()
+
+
+def test_skewed_full_size(kp):
+    """The real-data-like skewed workload (N=1,048,576, D=32, K=128, G=13;
+    power-law cluster sizes, feature scales over three orders of magnitude
+    far from the origin, integer features, outliers, duplicates), seeded by
+    k-means++ on the GPU (indices equal to O4's), then the sampled lockstep."""
+    w = synth.skewed_mixture()
+    Xd = torch.from_numpy(w.X).cuda()
+    C0 = torch.empty(w.K, w.D, dtype=torch.float32, device="cuda")
+    idx = torch.empty(w.K, dtype=torch.int64, device="cuda")
+    kp.kmeans_init_kmeanspp(Xd, w.N, w.D, w.K, w.meta["pp_u"], C0, idx)
+    X64 = w.X.astype(np.float64)
+    ref, _ = oracle.kmeanspp(X64, w.K, w.meta["pp_u"])
+    assert np.array_equal(idx.cpu().numpy(), ref)
+    for algo in (0, 1):
+        km = kp.KMeans(Xd, C0, w.G, algo=algo)
+        sampled_run(kp, km, X64, w.max_iter, w.tol, seed=11 + algo)
+        km.close()

@@ -251,6 +251,18 @@ def test_objective_far_from_origin(kp, offset, algo):
     assert all(s["objective"] < 200.0 * N * D for s in st)  # J is O(N D centre_range^2), not O(N D offset^2)
 
 
+def test_skewed_reduced_lockstep(kp):
+    """The skewed workload's recipe at N=65,536 (power-law sizes, features on
+    very different scales far from the origin, integer features, outliers,
+    duplicates), from k-means++ centres: every iteration checked, with bounds
+    on the filtered path throughout and with the default switch."""
+    w = synth.skewed_mixture(N=1 << 16)
+    idx, _ = oracle.kmeanspp(w.X.astype(np.float64), w.K, w.meta["pp_u"])
+    C0 = w.X[idx]
+    lockstep(kp, w.X, C0, w.G, 8)
+    lockstep(kp, w.X, C0, w.G, 8, check_bounds=True, dense_switch=1.0)
+
+
 def test_bounds_stay_valid(kp):
     w = synth.small_blobs(N=3000, D=16, K=24, G=5, seed=4)
     lockstep(kp, w.X, w.C0, w.G, 12, check_bounds=True, dense_switch=1.0)
