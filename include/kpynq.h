@@ -503,6 +503,19 @@ KM_API int kmeans_mlp_predict(const float *X, int64_t N, int32_t D, const float 
  * KM_EINVAL (NULL), KM_ENOMEM, KM_ECUDA; message in kmeans_last_error(NULL). */
 KM_API int kmeans_selftest_sqrt(int64_t *violations);
 
+/* Device self-test of the bounded waits: one thread waits on an mbarrier that
+ * nothing arrives at, giving up after `polls` bounded try-waits (each returns
+ * within a hardware time limit) exactly as the library's kernels do, records
+ * the time-out in a control block and returns.  Expected result: KM_ETIMEOUT,
+ * with the device still usable afterwards.  Errors: KM_EINVAL (polls outside
+ * [1, 65536]), KM_ENOMEM, KM_ECUDA; message in kmeans_last_error(NULL). */
+KM_API int kmeans_selftest_timeout(int32_t polls);
+
+/* Testing hook: after `after` more device allocations by contexts (>= 0),
+ * every further one fails as out of memory (KM_ENOMEM from the call that
+ * made it); a negative value switches the hook off.  Process-wide. */
+KM_API void kmeans_debug_fail_alloc(int64_t after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -155,8 +155,18 @@ cudaError_t lib_pool(int dev, cudaMemPool_t *out) {
     return cudaSuccess;
 }
 
+// Allocation-failure hook (kmeans_debug_fail_alloc): when >= 0, the number of
+// context allocations still allowed before each further one fails as out of
+// memory (a host-side stand-in for a full device, for testing KM_ENOMEM)
+std::atomic<long long> g_alloc_budget{-1};
+
 template <class T>
 cudaError_t dalloc(kmeans_ctx *c, T **p, size_t count) {
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) return cudaErrorMemoryAllocation;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
     cudaMemPool_t pool;
     cudaError_t e = lib_pool(c->dev, &pool);
     if (e != cudaSuccess) return e;
@@ -1056,6 +1066,8 @@ KM_API int kmeans_mlp_predict(const float *X, int64_t N, int32_t D, const float 
 }
 
 KM_API const char *kmeans_last_error(const kmeans_ctx *c) { return c ? c->err : g_init_error; }
+
+KM_API void kmeans_debug_fail_alloc(int64_t after) { g_alloc_budget.store(after < 0 ? -1 : after); }
 
 KM_API int64_t kmeans_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 

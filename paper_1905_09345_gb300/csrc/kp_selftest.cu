@@ -27,6 +27,17 @@ __global__ void k_selftest_sqrt(unsigned long long *violations) {
     if ((threadIdx.x & 31) == 0 && bad) atomicAdd(violations, bad);
 }
 
+// One thread waits, with the bounded mbarrier wait every kernel of the library
+// uses, on a barrier that expects one arrival that never comes; when the wait
+// gives up it records KM_ETIMEOUT in the control block's error word, the way
+// the library's kernels do, and returns.  Nothing is in flight on the barrier.
+__global__ void k_selftest_timeout(uint32_t polls, Ctrl *ctrl) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    if (!mbar_wait_bounded(&bar, 0, polls)) atomicExch(&ctrl->err, (int)KM_ETIMEOUT);
+}
+
 int fail_msg(int code, const char *msg) {
     set_thread_error(msg);
     return code;
@@ -62,6 +73,33 @@ KM_API int kmeans_selftest_sqrt(int64_t *violations) {
         return fail_msg(KM_ECUDA, cudaGetErrorString(e));
     }
     *violations = (int64_t)h;
+    return KM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+KM_API int kmeans_selftest_timeout(int32_t polls) {
+    if (polls < 1 || polls > (1 << 16)) return fail_msg(KM_EINVAL, "polls out of range [1, 65536]");
+    Ctrl *d = nullptr;
+    if (cudaMalloc(&d, sizeof(Ctrl)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(KM_ENOMEM, "cudaMalloc failed");
+    }
+    Ctrl h;
+    cudaError_t e = cudaMemset(d, 0, sizeof(Ctrl));
+    if (e == cudaSuccess) {
+        k_selftest_timeout<<<1, 32>>>((uint32_t)polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(KM_ECUDA, cudaGetErrorString(e));
+    }
+    if (h.err == KM_ETIMEOUT) return fail_msg(KM_ETIMEOUT, "a bounded device-side wait gave up");
     return KM_OK;
 }
 

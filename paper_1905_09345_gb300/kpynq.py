@@ -129,6 +129,10 @@ def lib():
         L.kmeans_shard_update.restype = ctypes.c_int
         L.kmeans_init_kmeanspp.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp]
         L.kmeans_init_kmeanspp.restype = ctypes.c_int
+        L.kmeans_selftest_timeout.argtypes = [i32]
+        L.kmeans_selftest_timeout.restype = ctypes.c_int
+        L.kmeans_debug_fail_alloc.argtypes = [i64]
+        L.kmeans_debug_fail_alloc.restype = None
         u64, f32 = ctypes.c_uint64, ctypes.c_float
         L.kmeans_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, u64, vp]
         L.kmeans_mlp_create.restype = ctypes.c_int
@@ -342,6 +346,16 @@ def kmeans_init_kmeanspp(X, N: int, D: int, K: int, u, centroids, indices=None, 
     """k-means++ seeding: K centres of X (device) from the K uniforms u."""
     st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().kmeans_init_kmeanspp(_addr(X), N, D, K, _addr(u), _addr(centroids), _addr(indices), st), None)
+
+
+def kmeans_selftest_timeout(polls: int) -> int:
+    """The bounded-wait self-test's status (KM_ETIMEOUT expected); does not raise."""
+    return lib().kmeans_selftest_timeout(polls)
+
+
+def kmeans_debug_fail_alloc(after: int) -> None:
+    """Make context allocations fail after `after` more (negative: off)."""
+    lib().kmeans_debug_fail_alloc(after)
 
 
 def kmeans_destroy(ctx) -> None:

@@ -124,6 +124,8 @@ def test_null_context_calls(L):
     assert "hidden" in L.kmeans_last_error(None)
     lib.kmeans_selftest_sqrt.restype = __import__("ctypes").c_int
     assert lib.kmeans_selftest_sqrt(None) == L.KM_EINVAL
+    assert L.kmeans_selftest_timeout(0) == L.KM_EINVAL
+    assert L.kmeans_selftest_timeout(1 << 17) == L.KM_EINVAL
 
 
 def test_default_options(L):
