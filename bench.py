@@ -639,7 +639,8 @@ def run_ours(args):
         for name, fn in (("highdim4m", lambda: highdim_record(args, dev, fs, fw)),
                          ("batched512", lambda: batched_record(args, dev, steps=fs, warmup=fw)),
                          ("proposal8m", lambda: proposal_record(args, dev, log=log, steps=fs, warmup=fw)),
-                         ("skewed1m", lambda: skewed_record(args, dev, fs, fw))):
+                         ("skewed1m", lambda: skewed_record(args, dev, fs, fw)),
+                         ("grouping_aniso1m", lambda: grouping_record(args, dev, fs, fw))):
             t0 = time.perf_counter()
             try:
                 rec = fn()
@@ -676,6 +677,12 @@ def run_ours(args):
                              "iters": statistics.mean(li32), "dense": "FP32 CUDA cores"},
         "vs_plain_lloyd_fp32": value / lloyd32_value,
         "paths": [s["path"] for s in stats],
+        "filter_counts": {"n_survivors": [s["n_survivors"] for s in stats],
+                          "n_scanned": [s["n_scanned"] for s in stats],
+                          "n_dist": [s["n_dist"] for s in stats],
+                          "what": "per iteration: points the global filter did not keep, points still "
+                                  "unresolved after tightening u (then group and point filters), distances "
+                                  "evaluated (K per point in a dense pass)"},
         "kernel_breakdown": breakdown,
         "forms": forms,
     }
@@ -845,6 +852,47 @@ def skewed_record(args, dev, steps, warmup) -> dict:
             "vs_plain_lloyd": out["filtered"]["value"] / out["plain_lloyd"]["value"]}
 
 
+def grouping_record(args, dev, steps, warmup) -> dict:
+    """The anisotropic 1M job (G = 26) with contiguous and with clustered
+    groups (Lloyd over the initial centroids): time per fit and the fraction
+    of distance evaluations skipped, with the default switch and with the
+    filters alone after iteration 0."""
+    import torch
+    from paper_1905_09345_gb300 import kpynq
+    w = make_workload(argparse.Namespace(workload="aniso1m", n=None), 0)
+    X = device_points(w, dev)
+    C0 = torch.from_numpy(w.C0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    lab = torch.empty(w.N, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for grouping, name in ((kpynq.KM_GROUP_CONTIGUOUS, "contiguous"), (kpynq.KM_GROUP_CLUSTERED, "clustered")):
+        for switch in (0.0, 1.0):
+            km = kpynq.KMeans(X, C0, w.G, stream=stream, dense_switch=switch, grouping=grouping)
+            ng = km.groups()
+            times, iters = [], []
+            for i in range(warmup + steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                km.reset(C0)
+                r = km.fit(w.max_iter, w.tol, lab, with_stats=False)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= warmup:
+                    times.append(e0.elapsed_time(e1))
+                    iters.append(r.n_iter)
+            st = km.stats(0, iters[-1])
+            km.close()
+            later = [s_ for s_ in st if s_["iter"] > 0]
+            rows.append({"grouping": name, "groups": ng, "switch": "default" if switch == 0.0 else "filters only",
+                         "ms_per_fit": statistics.mean(times), "iters": iters[-1],
+                         "skip_fraction": 1.0 - sum(s_["n_dist"] for s_ in st) / (w.N * w.K * len(st)),
+                         "skip_fraction_iters_ge_1": 1.0 - sum(s_["n_dist"] for s_ in later) /
+                         max(1, w.N * w.K * len(later))})
+    return {"config": {"workload": w.name, "N": w.N, "D": w.D, "K": w.K, "G": w.G}, "rows": rows}
+
+
 def highdim_record(args, dev, steps, warmup) -> dict:
     """The high-dimension job (N=4,194,304, D=128, K=1024, G=103, bfloat16
     storage, 30 iterations): the filtered method and plain Lloyd, both with
@@ -916,8 +964,12 @@ def run_gsweep(args):
     rows = []
     with ClockSampler(gpu_uuid()) as clk:
         for G in sorted({1, max(1, K // 20), max(1, K // 10), max(1, K // 5), K}):
-            for switch, label in ((0.0, "default switch"), (1.0, "filters only")):
-                km = kpynq.KMeans(X, C0, G, stream=stream, dense_switch=switch)
+            for grouping, switch, label in ((0, 0.0, "default switch"), (0, 1.0, "filters only"),
+                                            (1, 0.0, "clustered, default switch"),
+                                            (1, 1.0, "clustered, filters only")):
+                if grouping and G in (1, K):
+                    continue  # one group, or one centroid per group: the same as contiguous
+                km = kpynq.KMeans(X, C0, G, stream=stream, dense_switch=switch, grouping=grouping)
                 times, iters, nd = [], [], 0
                 for i in range(args.warmup + args.steps):
                     flush.zero_()

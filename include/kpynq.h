@@ -76,9 +76,19 @@ enum {
     KM_ALGO_LLOYD = 1     /* plain Lloyd: every distance, every iteration */
 };
 
-/* kmeans_options.grouping: how the K centroids form the G groups */
+/* kmeans_options.grouping: how the K centroids form the G groups (labels
+ * never depend on it; how much the filters skip does) */
 enum {
-    KM_GROUP_CONTIGUOUS = 0 /* centroid j -> group floor(j * G / K) */
+    KM_GROUP_CONTIGUOUS = 0, /* centroid j -> group floor(j * G / K) */
+    KM_GROUP_CLUSTERED = 1   /* groups of nearby centroids: plain Lloyd over the K
+                                initial centroids, seeded by their first G rows, 5
+                                iterations (the library's own kernels); a centroid
+                                joins the group of its nearest centre (lowest index
+                                on ties).  Groups left empty are dropped, so fewer
+                                than G groups may result; bound rows (kmeans_get_bounds)
+                                then hold the remaining groups in the order of
+                                their seeds.  Labels and centroids are always in
+                                the caller's numbering. */
 };
 
 /* kmeans_options.dtype: storage type of X.  init_centroids and every output
@@ -236,6 +246,11 @@ KM_API int kmeans_reset(kmeans_ctx *ctx, const float *init_centroids);
  * kmeans_options.profile is set.  kind: KM_KERNEL_*.  launches / ms nullable.
  */
 KM_API int kmeans_get_profile(kmeans_ctx *ctx, int32_t kind, int64_t *launches, double *ms);
+
+/* The grouping in use: grp[k] (nullable, K int32, host or device) = group of
+ * centroid k (the caller's numbering), *n_groups (nullable) = the number of
+ * groups (G, or fewer for a clustered grouping that left groups empty). */
+KM_API int kmeans_get_groups(kmeans_ctx *ctx, int32_t *grp, int32_t *n_groups);
 
 /* Number of iterations run so far on this context. */
 KM_API int kmeans_get_iteration(const kmeans_ctx *ctx, int32_t *t);

@@ -290,6 +290,53 @@ int ensure_tables(kmeans_ctx *c, int need) {
     return KM_OK;
 }
 
+// Centroids and labels in the caller's numbering (the context may hold its
+// centroids in another order; Params::orig maps internal -> caller index).
+cudaError_t centroids_in(kmeans_ctx *c, const float *src) {
+    const Params &p = c->p;
+    cudaStream_t s = c->stream;
+    if (!p.orig)
+        return cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, src, (size_t)p.D * 4, (size_t)p.D * 4, p.K, cudaMemcpyDefault,
+                                 s);
+    const float *d = src;
+    float *tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!is_device_ptr(src)) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)p.K * p.D * 4, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, (size_t)p.K * p.D * 4, cudaMemcpyDefault, s);
+        d = tmp;
+    }
+    if (e == cudaSuccess) e = launch_rows_in(d, p.D, p.K, p.Dp, p.orig, p.C, s, c->num_sms);
+    if (tmp) cudaFreeAsync(tmp, s);
+    return e;
+}
+cudaError_t centroids_out(kmeans_ctx *c, float *dst, cudaStream_t s) {
+    const Params &p = c->p;
+    if (!p.orig)
+        return cudaMemcpy2DAsync(dst, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K, cudaMemcpyDefault,
+                                 s);
+    const bool dev = is_device_ptr(dst);
+    float *out = dst;
+    cudaError_t e = cudaSuccess;
+    if (!dev) e = cudaMallocAsync(reinterpret_cast<void **>(&out), (size_t)p.K * p.D * 4, s);
+    if (e == cudaSuccess) e = launch_rows_out(p.C, p.Dp, p.D, p.K, p.orig, out, s, c->num_sms);
+    if (!dev && e == cudaSuccess) e = cudaMemcpyAsync(dst, out, (size_t)p.K * p.D * 4, cudaMemcpyDeviceToHost, s);
+    if (!dev && out) cudaFreeAsync(out, s);
+    return e;
+}
+cudaError_t labels_out(kmeans_ctx *c, int32_t *dst, cudaStream_t s) {
+    const Params &p = c->p;
+    if (!p.orig) return cudaMemcpyAsync(dst, p.label, (size_t)p.N * 4, cudaMemcpyDefault, s);
+    const bool dev = is_device_ptr(dst);
+    int32_t *out = dst;
+    cudaError_t e = cudaSuccess;
+    if (!dev) e = cudaMallocAsync(reinterpret_cast<void **>(&out), (size_t)p.N * 4, s);
+    if (e == cudaSuccess) e = launch_labels_out(p.label, p.N, p.orig, p.K, out, s, c->num_sms);
+    if (!dev && e == cudaSuccess) e = cudaMemcpyAsync(dst, out, (size_t)p.N * 4, cudaMemcpyDeviceToHost, s);
+    if (!dev && out) cudaFreeAsync(out, s);
+    return e;
+}
+
 // One assignment (dense when `dense`, filtered otherwise), stream-ordered.
 // Cluster statistics after an assignment: the full recompute (when the device
 // chooses it) and the incremental moves (otherwise).
@@ -516,7 +563,8 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     kmeans_default_options(&o);
     if (opt) o = *opt;
     if (o.algo != KM_ALGO_FILTERED && o.algo != KM_ALGO_LLOYD) return set_err(nullptr, KM_EINVAL, "unknown algo %d", o.algo);
-    if (o.grouping != KM_GROUP_CONTIGUOUS) return set_err(nullptr, KM_EINVAL, "unknown grouping %d", o.grouping);
+    if (o.grouping != KM_GROUP_CONTIGUOUS && o.grouping != KM_GROUP_CLUSTERED)
+        return set_err(nullptr, KM_EINVAL, "unknown grouping %d", o.grouping);
     if (o.dense != KM_DENSE_AUTO && o.dense != KM_DENSE_FP32) return set_err(nullptr, KM_EINVAL, "unknown dense %d", o.dense);
     if (!(o.dense_switch >= 0.0f)) return set_err(nullptr, KM_EINVAL, "dense_switch must be >= 0");
     if (o.dtype != KM_DTYPE_F32 && o.dtype != KM_DTYPE_BF16) return set_err(nullptr, KM_EINVAL, "unknown dtype %d", o.dtype);
@@ -551,6 +599,56 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     c->smem_optin = (size_t)optin;
     INIT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     INIT_CUDA(cudaMallocHost(&c->ctrl_host, sizeof(Ctrl)));
+
+    // clustered grouping: plain Lloyd over the K initial centroids (this
+    // library's own kernels, an inner context), seeded by their first G rows,
+    // 5 iterations; empty groups are dropped and the centroids are ordered
+    // group by group (ascending caller index within a group), so that every
+    // kernel sees each group as a run of indices.  Ties between equal
+    // distances are broken by the caller's index (Params::orig).
+    std::vector<int32_t> cl_orig, cl_grp, cl_start;
+    if (o.grouping == KM_GROUP_CLUSTERED) {
+        kmeans_options go;
+        kmeans_default_options(&go);
+        go.algo = KM_ALGO_LLOYD;
+        go.stream = o.stream;
+        kmeans_ctx *gc = nullptr;
+        rc = kmeans_init(&gc, init_centroids, K, D, G, 1, init_centroids, &go);
+        if (rc) {
+            set_err(c, rc, "grouping: %s", g_init_error);
+            return fail(rc);
+        }
+        std::vector<int32_t> lab(K);
+        rc = kmeans_fit(gc, 5, 0.0, lab.data(), nullptr, nullptr, nullptr);
+        if (rc) set_err(c, rc, "grouping: %s", kmeans_last_error(gc));
+        kmeans_destroy(gc);
+        if (rc) return fail(rc);
+        std::vector<int32_t> cnt(G, 0), newid(G, -1);
+        for (int k = 0; k < K; ++k) {
+            if ((unsigned)lab[k] >= (unsigned)G) {
+                set_err(c, KM_ECUDA, "grouping produced a label out of range");
+                return fail(KM_ECUDA);
+            }
+            ++cnt[lab[k]];
+        }
+        int ge = 0;
+        for (int g = 0; g < G; ++g)
+            if (cnt[g]) newid[g] = ge++;
+        cl_start.assign(ge + 1, 0);
+        for (int g = 0; g < G; ++g)
+            if (cnt[g]) cl_start[newid[g] + 1] = cnt[g];
+        for (int g = 0; g < ge; ++g) cl_start[g + 1] += cl_start[g];
+        std::vector<int32_t> pos(cl_start.begin(), cl_start.end() - 1);
+        cl_orig.resize(K);
+        cl_grp.resize(K);
+        for (int k = 0; k < K; ++k) {
+            const int g = newid[lab[k]];
+            const int kk = pos[g]++;
+            cl_orig[kk] = k;
+            cl_grp[kk] = g;
+        }
+        G = ge;
+    }
 
     Params &p = c->p;
     p.N = N;
@@ -641,8 +739,14 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
 
     cudaStream_t s = c->stream;
     INIT_CUDA(cudaMemsetAsync(p.C, 0, (size_t)K * p.Dp * 4, s));
-    INIT_CUDA(cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)D * 4, (size_t)D * 4, K,
-                                cudaMemcpyDefault, s));
+    if (!cl_orig.empty()) {
+        int32_t *orig;
+        INIT_CUDA(dalloc(c, &orig, (size_t)K));
+        INIT_CUDA(cudaMemcpyAsync(orig, cl_orig.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
+        INIT_CUDA(cudaStreamSynchronize(s));  // cl_orig is a host temporary
+        p.orig = orig;
+    }
+    INIT_CUDA(centroids_in(c, init_centroids));
     INIT_CUDA(cudaMemcpyAsync(p.R, p.C, (size_t)K * p.Dp * 4, cudaMemcpyDeviceToDevice, s));
     INIT_CUDA(cudaMemsetAsync(p.S, 0, (size_t)K * D * 8, s));
     INIT_CUDA(cudaMemsetAsync(p.Q, 0, (size_t)K * 8, s));
@@ -653,10 +757,15 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     INIT_CUDA(cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s));
     INIT_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(kmeans_iter_stats) * (kStatsCap + 1), s));
 
-    // contiguous grouping: centroid j -> floor(j G / K)
+    // contiguous grouping: centroid j -> floor(j G / K); clustered: the runs made above
     std::vector<int32_t> hg(K), hs(G + 1);
-    for (int j = 0; j < K; ++j) hg[j] = (int32_t)(((int64_t)j * G) / K);
-    for (int g = 0; g <= G; ++g) hs[g] = (int32_t)(((int64_t)g * K + G - 1) / G);
+    if (!cl_grp.empty()) {
+        hg = cl_grp;
+        hs = cl_start;
+    } else {
+        for (int j = 0; j < K; ++j) hg[j] = (int32_t)(((int64_t)j * G) / K);
+        for (int g = 0; g <= G; ++g) hs[g] = (int32_t)(((int64_t)g * K + G - 1) / G);
+    }
     INIT_CUDA(cudaMemcpyAsync(grp, hg.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
     INIT_CUDA(cudaMemcpyAsync(gstart, hs.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice, s));
 
@@ -852,10 +961,8 @@ KM_API int kmeans_fit(kmeans_ctx *c, int32_t max_iter, double tol, int32_t *labe
     }
     if ((rc = sync_and_check(c))) return rc;
     cudaStream_t s = c->stream;
-    if (labels) KP_CUDA(c, cudaMemcpyAsync(labels, p.label, (size_t)p.N * 4, cudaMemcpyDefault, s));
-    if (centroids)
-        KP_CUDA(c, cudaMemcpy2DAsync(centroids, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K,
-                                     cudaMemcpyDefault, s));
+    if (labels) KP_CUDA(c, labels_out(c, labels, s));
+    if (centroids) KP_CUDA(c, centroids_out(c, centroids, s));
     if (objective) KP_CUDA(c, cudaMemcpyAsync(objective, &p.ctrl->jfinal, 8, cudaMemcpyDefault, s));
     KP_CUDA(c, cudaStreamSynchronize(s));
     c->have_final = true;
@@ -872,7 +979,7 @@ KM_API int kmeans_get_labels(kmeans_ctx *c, int32_t *labels) {
     if (rc) return rc;
     if (!labels) return set_err(c, KM_EINVAL, "labels is NULL");
     DeviceGuard dg(c->dev);
-    KP_CUDA(c, cudaMemcpyAsync(labels, c->p.label, (size_t)c->p.N * 4, cudaMemcpyDefault, c->stream));
+    KP_CUDA(c, labels_out(c, labels, c->stream));
     KP_CUDA(c, cudaStreamSynchronize(c->stream));
     return KM_OK;
 }
@@ -882,9 +989,7 @@ KM_API int kmeans_get_centroids(kmeans_ctx *c, float *C) {
     if (rc) return rc;
     if (!C) return set_err(c, KM_EINVAL, "C is NULL");
     DeviceGuard dg(c->dev);
-    const Params &p = c->p;
-    KP_CUDA(c, cudaMemcpy2DAsync(C, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K, cudaMemcpyDefault,
-                                 c->stream));
+    KP_CUDA(c, centroids_out(c, C, c->stream));
     KP_CUDA(c, cudaStreamSynchronize(c->stream));
     return KM_OK;
 }
@@ -946,8 +1051,7 @@ KM_API int kmeans_reset(kmeans_ctx *c, const float *init_centroids) {
     cudaStream_t s = c->stream;
     if ((rc = sync_and_check(c))) return rc;
     c->kernels_base += (long long)c->ctrl_host->kernels;
-    KP_CUDA(c, cudaMemcpy2DAsync(p.C, (size_t)p.Dp * 4, init_centroids, (size_t)p.D * 4, (size_t)p.D * 4, p.K,
-                                 cudaMemcpyDefault, s));
+    KP_CUDA(c, centroids_in(c, init_centroids));
     KP_CUDA(c, cudaMemcpyAsync(p.R, p.C, (size_t)p.K * p.Dp * 4, cudaMemcpyDeviceToDevice, s));
     c->shard_pending = false;
     KP_CUDA(c, cudaMemsetAsync(p.S, 0, (size_t)p.K * p.D * 8, s));
@@ -976,6 +1080,22 @@ KM_API int kmeans_get_profile(kmeans_ctx *c, int32_t kind, int64_t *launches, do
     if (!c || kind < 0 || kind >= KM_KERNEL_KINDS) return KM_EINVAL;
     if (launches) *launches = c->prof_n[kind];
     if (ms) *ms = c->prof_ms[kind];
+    return KM_OK;
+}
+
+KM_API int kmeans_get_groups(kmeans_ctx *c, int32_t *grp, int32_t *n_groups) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    DeviceGuard dg(c->dev);
+    const Params &p = c->p;
+    if (n_groups) *n_groups = p.G;
+    if (!grp) return KM_OK;
+    std::vector<int32_t> g(p.K), o(p.K);
+    KP_CUDA(c, cudaMemcpy(g.data(), p.grp, (size_t)p.K * 4, cudaMemcpyDeviceToHost));
+    if (p.orig) KP_CUDA(c, cudaMemcpy(o.data(), p.orig, (size_t)p.K * 4, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> out(p.K);
+    for (int k = 0; k < p.K; ++k) out[p.orig ? o[k] : k] = g[k];
+    KP_CUDA(c, cudaMemcpy(grp, out.data(), (size_t)p.K * 4, cudaMemcpyDefault));
     return KM_OK;
 }
 
@@ -1016,6 +1136,8 @@ KM_API int kmeans_set_proposal(kmeans_ctx *c, const float *W1, const float *b1, 
     if (!none && (hidden < 1 || hidden > 256)) return set_err(c, KM_EINVAL, "hidden=%d outside [1, 256]", hidden);
     if (!none && (c->p.D > 256 || c->p.G > 512))
         return set_err(c, KM_EINVAL, "the proposal network takes D <= 256 and G <= 512");
+    if (!none && c->p.orig)
+        return set_err(c, KM_EINVAL, "the proposal predicts contiguous groups (KM_GROUP_CONTIGUOUS only)");
     DeviceGuard dg(c->dev);
     if ((rc = sync_and_check(c))) return rc;
     Params &p = c->p;
@@ -1301,10 +1423,8 @@ KM_API int kmeans_batch_get(kmeans_batch *b, int32_t i, int32_t *labels, float *
     const Params &p = c->p;
     cudaStream_t s = c->stream;
     cudaError_t e = cudaSuccess;
-    if (labels) e = cudaMemcpyAsync(labels, p.label, (size_t)p.N * 4, cudaMemcpyDefault, s);
-    if (e == cudaSuccess && centroids)
-        e = cudaMemcpy2DAsync(centroids, (size_t)p.D * 4, p.C, (size_t)p.Dp * 4, (size_t)p.D * 4, p.K,
-                              cudaMemcpyDefault, s);
+    if (labels) e = labels_out(c, labels, s);
+    if (e == cudaSuccess && centroids) e = centroids_out(c, centroids, s);
     if (e == cudaSuccess && objective) e = cudaMemcpyAsync(objective, &p.ctrl->jfinal, 8, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return batch_err(b, KM_ECUDA, "%s", cudaGetErrorString(e));

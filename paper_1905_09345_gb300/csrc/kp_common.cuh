@@ -112,6 +112,8 @@ struct Params {
     float *Dg;           // tcap x Gp
     float *Dm;           // tcap
     const int32_t *grp;  // K: group of each centroid
+    const int32_t *orig; // K: caller's index of each centroid (the context may order its
+                         // centroids so that every group is a run of indices); NULL: identity
     const int32_t *gstart;  // G + 1: centroids of group g are [gstart[g], gstart[g+1])
 
     int32_t *queue;      // N: survivors of the global filter, grouped by label bucket
@@ -224,6 +226,20 @@ __device__ __forceinline__ void warp_argmin(float &v, int &i) {
         float ov = __shfl_xor_sync(0xffffffffu, v, o);
         int oi = __shfl_xor_sync(0xffffffffu, i, o);
         if (ov < v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+}
+// the key that breaks ties between equal distances: the caller's index of
+// centroid c (the lowest wins); indices outside [0, K) (sentinels) keep their value
+__device__ __forceinline__ int tie_key(const Params &p, int c) {
+    return (p.orig && (unsigned)c < (unsigned)p.K) ? p.orig[c] : c;
+}
+// (value, index) minimum over the warp, ties to the lowest tie_key
+__device__ __forceinline__ void warp_argmin_d_key(double &v, int &i, const Params &p) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov < v || (ov == v && tie_key(p, oi) < tie_key(p, i))) { v = ov; i = oi; }
     }
 }
 __device__ __forceinline__ void warp_argmin_d(double &v, int &i) {
@@ -383,6 +399,13 @@ cudaError_t launch_kmeanspp(const float *X, int64_t N, int D, int K, const doubl
                             double *dmin, unsigned long long *bsum, void *state, cudaStream_t s, int num_sms,
                             long long *err_out);
 size_t kmeanspp_state_bytes();
+// the caller's centroid numbering (kp_update.cu)
+cudaError_t launch_labels_out(const int32_t *label, int64_t N, const int32_t *orig, int K, int32_t *out,
+                              cudaStream_t s, int num_sms);
+cudaError_t launch_rows_out(const float *C, int Dp, int D, int K, const int32_t *orig, float *out, cudaStream_t s,
+                            int num_sms);
+cudaError_t launch_rows_in(const float *in, int D, int K, int Dp, const int32_t *orig, float *C, cudaStream_t s,
+                           int num_sms);
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t s, int num_sms);
 cudaError_t launch_bf16_to_f32(const uint16_t *in, int64_t n, float *out, cudaStream_t s, int num_sms);
 

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_assign(Params p, int fi
                     float s = sqdist_again<DP>(p, x, n, c);
                     if (!unresolved(s1_ref, s, p)) continue;
                     double d64 = dist2_f64(p.X + n * p.D, p.C + (size_t)c * p.Dp, p.D);
-                    if (d64 < bd) { bd = d64; bi = c; bs = s; }
+                    if (d64 < bd || (d64 == bd && tie_key(p, c) < tie_key(p, bi))) { bd = d64; bi = c; bs = s; }
                 }
                 my_recheck += 1;
                 if (bi != best) {

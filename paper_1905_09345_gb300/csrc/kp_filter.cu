@@ -476,11 +476,11 @@ __global__ void __launch_bounds__(512, 2) k_survivor(Params p, int respect_done,
                     float s = sq[c];
                     if (s >= 0.f && unresolved(s_best, s, p)) {
                         double d64 = dist2_f64(xs, Cs + (size_t)c * p.Dp, D);
-                        if (d64 < bd64 || (d64 == bd64 && c < bi)) { bd64 = d64; bi = c; }
+                        if (d64 < bd64 || (d64 == bd64 && tie_key(p, c) < tie_key(p, bi))) { bd64 = d64; bi = c; }
                     }
                 }
             }
-            warp_argmin_d(bd64, bi);
+            warp_argmin_d_key(bd64, bi, p);
             best = bi;
             s_best = sq[bi];
             c_recheck += 1;

@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kSettleThreads, 1) k_settle(Params p, int firs
                     for_groups([&](int c0, int c1) __attribute__((always_inline)) {
                         for (int col = c0 + sl; col < c1; col += SUB) {
                             const double d64 = settle_fp64(xg, Cb + (size_t)col * cst, D);
-                            if (d64 < bd || (d64 == bd && col < bj)) {
+                            if (d64 < bd || (d64 == bd && tie_key(p, col) < tie_key(p, bj))) {
                                 bd = d64;
                                 bj = col;
                             }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kSettleThreads, 1) k_settle(Params p, int firs
                     for (int o = SUB / 2; o > 0; o >>= 1) {
                         const double ov = __shfl_xor_sync(smask, bd, o, SUB);
                         const int oi = __shfl_xor_sync(smask, bj, o, SUB);
-                        if (ov < bd || (ov == bd && oi < bj)) {
+                        if (ov < bd || (ov == bd && tie_key(p, oi) < tie_key(p, bj))) {
                             bd = ov;
                             bj = oi;
                         }
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle_t(Params p, int fi
                 }
                 if (!cand || !unresolved(s1r, settle_fp32_mem<D>(xg, Cs + (size_t)c * SD), p)) continue;
                 const double d64 = settle_fp64(xg, Cs + (size_t)c * SD, D);
-                if (d64 < bd) {
+                if (d64 < bd || (d64 == bd && tie_key(p, c) < tie_key(p, bj))) {
                     bd = d64;
                     bj = c;
                 }
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kSettleThreads, 2) k_settle_t(Params p, int fi
             for (int o = 16; o > 0; o >>= 1) {
                 const double ov = __shfl_xor_sync(0xffffffffu, bd, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bj, o);
-                if (ov < bd || (ov == bd && oi < bj)) {
+                if (ov < bd || (ov == bd && tie_key(p, oi) < tie_key(p, bj))) {
                     bd = ov;
                     bj = oi;
                 }

@@ -164,7 +164,7 @@ __device__ __forceinline__ int settle_warp(const Params &p, const float *Cs, con
         const float s = sqdist_mem<DP>(p, xg, Cs + (size_t)c * p.Dp);
         if (!unresolved(s1, s, p)) continue;
         const double d = dist2_f64_mem<DP>(p, xg, Cs + (size_t)c * p.Dp);
-        if (d < bd) {
+        if (d < bd || (d == bd && tie_key(p, c) < tie_key(p, bi))) {
             bd = d;
             bi = c;
         }
@@ -173,7 +173,7 @@ __device__ __forceinline__ int settle_warp(const Params &p, const float *Cs, con
     for (int o = 16; o > 0; o >>= 1) {
         const double od = __shfl_xor_sync(0xffffffffu, bd, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (od < bd || (od == bd && oi < bi)) {
+        if (od < bd || (od == bd && tie_key(p, oi) < tie_key(p, bi))) {
             bd = od;
             bi = oi;
         }

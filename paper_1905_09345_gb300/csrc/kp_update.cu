@@ -251,6 +251,52 @@ __global__ void k_bf16_to_f32(const uint16_t *in, int64_t n, float *out) {
         out[i] = __uint_as_float((uint32_t)in[i] << 16);
 }
 
+// The caller's centroid numbering (a context may order its centroids group by
+// group): labels out[n] = orig[label[n]], centroid rows out[orig[k]] = C[k]
+// and C[k] = in[orig[k]].
+__global__ void k_labels_out(const int32_t *label, int64_t N, const int32_t *orig, int K, int32_t *out) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const int k = label[n];
+        out[n] = (unsigned)k < (unsigned)K ? orig[k] : k;
+    }
+}
+__global__ void k_rows_out(const float *C, int Dp, int D, int K, const int32_t *orig, float *out) {
+    const int64_t total = (int64_t)K * D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / D), d = (int)(i - (int64_t)k * D);
+        out[(int64_t)orig[k] * D + d] = C[(int64_t)k * Dp + d];
+    }
+}
+__global__ void k_rows_in(const float *in, int D, int K, int Dp, const int32_t *orig, float *C) {
+    const int64_t total = (int64_t)K * D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / D), d = (int)(i - (int64_t)k * D);
+        C[(int64_t)k * Dp + d] = in[(int64_t)orig[k] * D + d];
+    }
+}
+
+cudaError_t launch_labels_out(const int32_t *label, int64_t N, const int32_t *orig, int K, int32_t *out,
+                              cudaStream_t s, int num_sms) {
+    count_launch();
+    k_labels_out<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, (int64_t)num_sms * 8)), 256, 0,
+                   s>>>(label, N, orig, K, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_rows_out(const float *C, int Dp, int D, int K, const int32_t *orig, float *out, cudaStream_t s,
+                            int num_sms) {
+    count_launch();
+    k_rows_out<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)K * D + 255) / 256, (int64_t)num_sms * 8)),
+                 256, 0, s>>>(C, Dp, D, K, orig, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_rows_in(const float *in, int D, int K, int Dp, const int32_t *orig, float *C, cudaStream_t s,
+                           int num_sms) {
+    count_launch();
+    k_rows_in<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)K * D + 255) / 256, (int64_t)num_sms * 8)),
+                256, 0, s>>>(in, D, K, Dp, orig, C);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bf16_to_f32(const uint16_t *in, int64_t n, float *out, cudaStream_t s, int num_sms) {
     count_launch();
     k_bf16_to_f32<<<num_sms * 8, 256, 0, s>>>(in, n, out);

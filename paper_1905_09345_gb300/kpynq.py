@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libkpynq.so")
 KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ESTATE = 0, -1, -2, -3, -4, -5
 KM_ALGO_FILTERED, KM_ALGO_LLOYD = 0, 1
 KM_DTYPE_F32, KM_DTYPE_BF16 = 0, 1
-KM_GROUP_CONTIGUOUS = 0
+KM_GROUP_CONTIGUOUS, KM_GROUP_CLUSTERED = 0, 1
 KM_DENSE_AUTO, KM_DENSE_FP32 = 0, 1
 KM_PATH_FILTERED, KM_PATH_DENSE_FP32, KM_PATH_DENSE_TC = 0, 1, 2
 (KM_KERNEL_DENSE, KM_KERNEL_MOVES, KM_KERNEL_FILTER, KM_KERNEL_SURVIVOR, KM_KERNEL_UPDATE, KM_KERNEL_OTHER,
@@ -91,6 +91,8 @@ def lib():
         L.kmeans_get_stats.restype = ctypes.c_int
         L.kmeans_get_bounds.argtypes = [vp, vp, vp, vp]
         L.kmeans_get_bounds.restype = ctypes.c_int
+        L.kmeans_get_groups.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.kmeans_get_groups.restype = ctypes.c_int
         L.kmeans_get_iteration.argtypes = [vp, ctypes.POINTER(i32)]
         L.kmeans_get_iteration.restype = ctypes.c_int
         L.kmeans_get_kernel_count.argtypes = [vp, ctypes.POINTER(i64)]
@@ -267,6 +269,13 @@ def kmeans_get_bounds(ctx, u=None, lbg=None, lb=None) -> None:
     _check(lib().kmeans_get_bounds(ctx, _addr(u), _addr(lbg), _addr(lb)), ctx)
 
 
+def kmeans_get_groups(ctx, grp=None) -> int:
+    """Fills grp (K int32) with each centroid's group; returns the number of groups."""
+    n = ctypes.c_int32()
+    _check(lib().kmeans_get_groups(ctx, _addr(grp), ctypes.byref(n)), ctx)
+    return n.value
+
+
 def kmeans_get_iteration(ctx) -> int:
     t = ctypes.c_int32()
     _check(lib().kmeans_get_iteration(ctx, ctypes.byref(t)), ctx)
@@ -390,11 +399,12 @@ class KMeans:
 
     def __init__(self, X, C0, G: int, *, algo: int = KM_ALGO_FILTERED, stream=None, validate: bool = False,
                  profile: bool = False, dense: int = KM_DENSE_AUTO, dense_switch: float = 0.0,
-                 dtype: int | None = None):
+                 dtype: int | None = None, grouping: int = KM_GROUP_CONTIGUOUS):
         N, D = X.shape
         K = C0.shape[0]
         opt = kmeans_default_options()
         opt.algo = algo
+        opt.grouping = grouping
         opt.validate = int(validate)
         opt.profile = int(profile)
         opt.dense = dense
@@ -427,6 +437,10 @@ class KMeans:
             self.close()
         except Exception:
             pass
+
+    def groups(self, grp=None) -> int:
+        """Number of groups; fills grp (K int32) with each centroid's group."""
+        return kmeans_get_groups(self.ctx, grp)
 
     def reset(self, C0):
         """Restart from new initial centroids (no allocation)."""
@@ -528,7 +542,8 @@ class KMeansBatch:
     the autotuner's cache file (None: the library's default switch)."""
 
     def __init__(self, problems, algo: int = KM_ALGO_FILTERED, stream=None, dense: int = KM_DENSE_AUTO,
-                 dense_switch: float = 0.0, tune_cache: str | None = None, dtype: int | None = None):
+                 dense_switch: float = 0.0, tune_cache: str | None = None, dtype: int | None = None,
+                 grouping: int = KM_GROUP_CONTIGUOUS):
         arr = (kmeans_problem * len(problems))()
         self._keep = []
         for i, (X, C0, G) in enumerate(problems):
@@ -539,6 +554,7 @@ class KMeansBatch:
         opt = kmeans_options()
         lib().kmeans_default_options(ctypes.byref(opt))
         opt.algo = algo
+        opt.grouping = grouping
         opt.dense = dense
         opt.dense_switch = dense_switch
         opt.dtype = _dtype_of(problems[0][0], dtype) if problems else KM_DTYPE_F32

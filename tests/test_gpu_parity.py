@@ -82,17 +82,21 @@ def tc_expected(D, K, G, smem=232448, algo=0):
     return fixed + 2 * 2 * na * 128 * 128 <= smem
 
 
-def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None, dense=0, dense_switch=0.0):
+def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None, dense=0, dense_switch=0.0, grouping=0):
     """Run `iters` iterations in lockstep with the oracle; returns the list of
     per-iteration GPU stats."""
     N, D = X.shape
     K = C0.shape[0]
-    km = kp.KMeans(dev(X), dev(C0), G, algo=algo, dense=dense, dense_switch=dense_switch)
+    km = kp.KMeans(dev(X), dev(C0), G, algo=algo, dense=dense, dense_switch=dense_switch, grouping=grouping)
     X64 = X.astype(np.float64)
     prev = None
     stats = []
     near = 0
-    grp = oracle.contiguous_groups(K, G)
+    if grouping == kp.KM_GROUP_CLUSTERED:  # the library's grouping, in the caller's centroid numbering
+        grp = np.empty(K, np.int32)
+        G = km.groups(grp)
+    else:
+        grp = oracle.contiguous_groups(K, G)
     for t in range(iters):
         Ct = get_C(km)
         st = km.iterate()
@@ -127,7 +131,7 @@ def lockstep(kp, X, C0, G, iters, algo=0, check_bounds=False, report=None, dense
                 assert np.all(lb[:, g] <= m * (1 + 1e-12)), f"t={t}: group {g} lower bound above distance"
         if t > 0 and algo == 0 and dense_switch >= 1.0:
             assert st["path"] == kp.KM_PATH_FILTERED, (t, st["path"])
-        if t == 0 or algo == kp.KM_ALGO_LLOYD:
+        if (t == 0 or algo == kp.KM_ALGO_LLOYD) and grouping == kp.KM_GROUP_CONTIGUOUS:
             want = kp.KM_PATH_DENSE_TC if (dense == 0 and tc_expected(D, K, G, algo=algo)) else kp.KM_PATH_DENSE_FP32
             assert st["path"] == want, (t, st["path"], want)
         stats.append(st)
@@ -261,6 +265,74 @@ def test_skewed_reduced_lockstep(kp):
     C0 = w.X[idx]
     lockstep(kp, w.X, C0, w.G, 8)
     lockstep(kp, w.X, C0, w.G, 8, check_bounds=True, dense_switch=1.0)
+
+
+CLUSTERED = [(3000, 16, 24, 5, 8, 0), (5000, 64, 256, 26, 6, 0), (4000, 128, 300, 30, 4, 0),
+             (3001, 32, 600, 60, 4, 0), (2000, 8, 40, 8, 8, 1)]
+
+
+@pytest.mark.parametrize("N,D,K,G,iters,dense", CLUSTERED, ids=[f"N{c[0]}_D{c[1]}_K{c[2]}_G{c[3]}_e{c[5]}" for c in CLUSTERED])
+def test_clustered_grouping_lockstep(kp, N, D, K, G, iters, dense):
+    """Groups of nearby centroids (KM_GROUP_CLUSTERED): the context orders its
+    centroids group by group, yet labels (exact, in the caller's numbering),
+    centroids and objective equal the oracle's every iteration, and every
+    group bound holds for the library's groups -- on the survivor kernels for
+    D <= 64 and D > 64, both tensor-core engines and the FP32 engine."""
+    rng = np.random.default_rng(N + K)
+    X, _ = synth.gaussian_mixture(rng, N, D, max(2, K // 2), centre_range=6.0, scale="fixed", scale_args=(1.0,))
+    C0 = synth.sample_init(rng, X, K)
+    lockstep(kp, X, C0, G, iters, grouping=kp.KM_GROUP_CLUSTERED, dense=dense, check_bounds=N * K <= 1_500_000,
+             dense_switch=1.0)
+    lockstep(kp, X, C0, G, iters, grouping=kp.KM_GROUP_CLUSTERED, dense=dense)
+
+
+def test_clustered_grouping_equals_oracle(kp):
+    """The library's clustered grouping (Lloyd over the centroids with its own
+    kernels) is the oracle's, with empty groups dropped and the rest numbered
+    in the order of their seeds; well-separated centroid clouds, so no group
+    assignment is a near-tie."""
+    rng = np.random.default_rng(12)
+    G, per, D = 10, 12, 8
+    clouds = rng.uniform(-50, 50, (G, D))
+    C0 = (clouds[rng.permutation(np.repeat(np.arange(G), per))] + rng.normal(0, 0.5, (G * per, D))).astype(np.float32)
+    X = np.concatenate([C0, C0 + rng.normal(0, 0.1, C0.shape).astype(np.float32)])
+    for Gq in (1, 4, 10, 30):
+        km = kp.KMeans(dev(X), dev(C0), Gq, grouping=kp.KM_GROUP_CLUSTERED)
+        grp = np.empty(C0.shape[0], np.int32)
+        ng = km.groups(grp)
+        km.close()
+        ref = oracle.clustered_groups(C0.astype(np.float64), Gq)
+        used = np.unique(ref)  # ascending seed index
+        ren = np.full(Gq, -1)
+        ren[used] = np.arange(len(used))
+        assert ng == len(used), (Gq, ng, len(used))
+        assert np.array_equal(grp, ren[ref]), Gq
+
+
+@pytest.mark.parametrize("D", [4, 64])
+def test_clustered_grouping_exact_ties(kp, D):
+    """Every centre given twice, the copies far apart in index order, with
+    groups of nearby centroids: the copies land in the same group but at
+    different positions of the context's order, and every point (equidistant
+    from both copies in every iteration) must take the copy with the lower
+    caller index."""
+    rng = np.random.default_rng(15)
+    k = 8
+    centres = np.zeros((k, 2), np.float32)
+    centres[:, 0] = np.arange(k) * 10 - 35
+    centres[:, 1] = rng.choice(np.arange(-40, 41, 10), size=k)
+    o = np.arange(-2, 3, dtype=np.float32)
+    off = np.stack(np.meshgrid(o, o), -1).reshape(-1, 2)
+    X = np.zeros((k * off.shape[0], D), np.float32)
+    X[:, :2] = (centres[:, None, :] + off[None]).reshape(-1, 2)
+    X = X[rng.permutation(X.shape[0])]
+    C0 = np.zeros((2 * k, D), np.float32)
+    perm = rng.permutation(k)
+    C0[:k, :2] = centres[perm]
+    C0[k:, :2] = centres[perm[::-1]]
+    for sw in (0.0, 1.0):
+        st = lockstep(kp, X, C0, 4, 4, dense_switch=sw, grouping=kp.KM_GROUP_CLUSTERED)
+        assert all(s["n_recheck"] > 0 for s in st)
 
 
 def test_bounds_stay_valid(kp):
