@@ -116,7 +116,11 @@ typedef struct {
                             engine, 0.9 without), >= 1 = never */
     int32_t dtype;       /* KM_DTYPE_*: storage type of X */
     int32_t pad0;        /* must be zero */
-    int64_t reserved[4]; /* must be zero */
+    int32_t surv_grab;   /* survivor queue schedule: entries a warp of the D <= 64
+                            survivor kernel claims at a time (a multiple of 32 in
+                            [32, 1024]; 0 = 32) */
+    int32_t pad1;        /* must be zero */
+    int64_t reserved[3]; /* must be zero */
 } kmeans_options;
 
 /* kmeans_options.dense: how dense passes (iteration 0, plain Lloyd) compute
@@ -376,11 +380,16 @@ typedef struct {
 
 /* Create the contexts of n_problems problems with the options opt (NULL:
  * defaults; profile must be 0; opt->stream is shared by all problems).
- * tune_cache (nullable): path of the autotuner's cache.  When given, the
- * dense/filtered switch of each size bucket (D, ceil log2 K, ceil log2 N) is
- * taken from the file, or chosen by timing short fits of the bucket's
- * largest problem with switches 0.5, 0.7, 0.9 and 1 (never) and written to
- * it.  Errors: KM_EINVAL (bad arguments), the codes of kmeans_init. */
+ * tune_cache (nullable): path of the autotuner's cache.  When given, each
+ * size bucket (D, ceil log2 K, ceil log2 N) takes its settings from the file,
+ * or has them chosen by timing short fits (10 iterations) of the bucket's
+ * largest problem, one setting at a time: the dense/filtered switch (0.5,
+ * 0.7, 0.9, 1 = never), then the dense engine (tensor cores or FP32 CUDA
+ * cores, when the tensor cores take the shape), then the survivor queue
+ * schedule (32, 64 or 128 entries claimed per warp); the choices are written
+ * to the file, one "D logK logN switch dense grab" line per bucket (lines
+ * of an older "D logK logN switch" form are read with the defaults for the
+ * rest).  Errors: KM_EINVAL (bad arguments), the codes of kmeans_init. */
 KM_API int kmeans_batch_init(kmeans_batch **out, int32_t n_problems, const kmeans_problem *problems,
                              const kmeans_options *opt, const char *tune_cache);
 
@@ -400,6 +409,11 @@ KM_API int kmeans_batch_reset(kmeans_batch *b);
 
 /* The dense/filtered switch the batch uses for problem i. */
 KM_API int kmeans_batch_get_switch(const kmeans_batch *b, int32_t i, float *dense_switch);
+
+/* All tuned settings of problem i (each nullable): the switch, the dense
+ * engine (KM_DENSE_*) and the survivor queue schedule (entries per claim). */
+KM_API int kmeans_batch_get_tuning(const kmeans_batch *b, int32_t i, float *dense_switch, int32_t *dense,
+                                   int32_t *surv_grab);
 
 KM_API void kmeans_batch_destroy(kmeans_batch *b);
 

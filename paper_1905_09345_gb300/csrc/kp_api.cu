@@ -568,9 +568,11 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     if (o.dense != KM_DENSE_AUTO && o.dense != KM_DENSE_FP32) return set_err(nullptr, KM_EINVAL, "unknown dense %d", o.dense);
     if (!(o.dense_switch >= 0.0f)) return set_err(nullptr, KM_EINVAL, "dense_switch must be >= 0");
     if (o.dtype != KM_DTYPE_F32 && o.dtype != KM_DTYPE_BF16) return set_err(nullptr, KM_EINVAL, "unknown dtype %d", o.dtype);
-    if (o.pad0) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
-    for (int i = 0; i < 4; ++i)
+    if (o.pad0 || o.pad1) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i]) return set_err(nullptr, KM_EINVAL, "reserved option fields must be zero");
+    if (o.surv_grab != 0 && (o.surv_grab < 32 || o.surv_grab > 1024 || o.surv_grab % 32 != 0))
+        return set_err(nullptr, KM_EINVAL, "surv_grab must be 0 or a multiple of 32 in [32, 1024]");
 
     kmeans_ctx *c = new (std::nothrow) kmeans_ctx();
     if (!c) return set_err(nullptr, KM_ENOMEM, "host allocation failed");
@@ -782,6 +784,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     // default switch: the tensor-core dense pass costs about as much as the
     // survivor kernel with 70% of the points surviving; the FP32 one more
     p.dense_frac = o.dense_switch > 0.0f ? o.dense_switch : (c->use_tc ? 0.7f : 0.9f);
+    p.surv_grab = o.surv_grab;
     if (c->use_tc && !filtered && K > 256) {
         // plain Lloyd with streamed centroid blocks: the pass still writes
         // group bounds, so that the exact settle of a row visits only the
@@ -1205,6 +1208,7 @@ struct kmeans_batch {
     std::vector<kmeans_ctx *> ctx;
     std::vector<float *> c0;         // device copies of the initial centroids
     std::vector<float> sw;           // dense switch chosen per problem
+    std::vector<int> dense, grab;    // dense engine and survivor queue schedule per problem
     cudaGraph_t graph = nullptr;     // every problem's fit, recorded once
     cudaGraphExec_t exec = nullptr;
     int rec_max_iter = -1;
@@ -1226,68 +1230,111 @@ int batch_err(kmeans_batch *b, int code, const char *fmt, ...) {
     return code;
 }
 
-// ---- autotuner: the dense/filtered switch per size bucket ----------------
+// ---- autotuner: settings per size bucket ----------------------------------
 // A bucket is (D, ceil log2 K, ceil log2 N).  For every bucket of the batch
-// the tuner runs a short fit (10 iterations) of the bucket's largest problem
-// once per candidate switch and keeps the fastest in points x iterations per
-// second; the choices are cached in a text file, one "D logK logN switch"
-// line per bucket, and read back on later runs.
+// the tuner times short fits (10 iterations) of the bucket's largest problem
+// and keeps the fastest in points x iterations per second, one setting at a
+// time: the dense/filtered switch, then the dense engine, then the survivor
+// queue schedule.  The choices are cached in a text file, one
+// "D logK logN switch dense grab" line per bucket, and read back later.
 struct TuneKey {
     int D, lk, ln;
     bool operator<(const TuneKey &o) const {
         return D != o.D ? D < o.D : (lk != o.lk ? lk < o.lk : ln < o.ln);
     }
 };
+struct TuneVal {
+    float sw;
+    int dense;
+    int grab;
+};
 int ceil_log2(int64_t v) {
     int l = 0;
     while (((int64_t)1 << l) < v) ++l;
     return l;
 }
-const float kTuneCandidates[] = {0.5f, 0.7f, 0.9f, 1.0f};
+const float kTuneSwitches[] = {0.5f, 0.7f, 0.9f, 1.0f};
+const int kTuneGrabs[] = {32, 64, 128};
 
-float tune_one(const kmeans_problem &pr, const kmeans_options &base, cudaStream_t s) {
-    float best_sw = 0.0f;
+// points x iterations per second of a 10-iteration fit with these settings
+// (< 0 when the settings do not run)
+double tune_rate(const kmeans_problem &pr, const kmeans_options &base, const TuneVal &v, cudaStream_t s,
+                 bool *used_tc) {
+    kmeans_options o = base;
+    o.dense_switch = v.sw;
+    o.dense = v.dense;
+    o.surv_grab = v.grab;
+    o.stream = s;
+    o.profile = 0;
+    kmeans_ctx *c = nullptr;
+    if (kmeans_init(&c, static_cast<const float *>(pr.X), pr.N, pr.D, pr.K, pr.G, pr.init_centroids, &o) != KM_OK)
+        return -1.0;
+    if (used_tc) *used_tc = c->use_tc;
+    int32_t n_it = 0;
+    kmeans_fit(c, 2, 0.0, nullptr, nullptr, nullptr, &n_it);  // warm-up: records the graph
+    kmeans_reset(c, pr.init_centroids);
+    cudaEvent_t a, z;
+    cudaEventCreate(&a);
+    cudaEventCreate(&z);
+    cudaEventRecord(a, s);
+    const int rc = kmeans_fit(c, 10, 0.0, nullptr, nullptr, nullptr, &n_it);
+    cudaEventRecord(z, s);
+    cudaEventSynchronize(z);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, z);
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    kmeans_destroy(c);
+    if (rc != KM_OK || ms <= 0.f) return -1.0;
+    return (double)pr.N * (n_it + 1) / ms;
+}
+
+TuneVal tune_one(const kmeans_problem &pr, const kmeans_options &base, cudaStream_t s) {
+    TuneVal best{0.0f, base.dense, 32};
     double best_rate = -1.0;
-    for (float sw : kTuneCandidates) {
-        kmeans_options o = base;
-        o.dense_switch = sw;
-        o.stream = s;
-        o.profile = 0;
-        kmeans_ctx *c = nullptr;
-        if (kmeans_init(&c, static_cast<const float *>(pr.X), pr.N, pr.D, pr.K, pr.G, pr.init_centroids, &o) != KM_OK)
-            return 0.0f;
-        int32_t n_it = 0;
-        kmeans_fit(c, 2, 0.0, nullptr, nullptr, nullptr, &n_it);  // warm-up: records the graph
-        kmeans_reset(c, pr.init_centroids);
-        cudaEvent_t a, z;
-        cudaEventCreate(&a);
-        cudaEventCreate(&z);
-        cudaEventRecord(a, s);
-        const int rc = kmeans_fit(c, 10, 0.0, nullptr, nullptr, nullptr, &n_it);
-        cudaEventRecord(z, s);
-        cudaEventSynchronize(z);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, z);
-        cudaEventDestroy(a);
-        cudaEventDestroy(z);
-        kmeans_destroy(c);
-        if (rc != KM_OK || ms <= 0.f) continue;
-        const double rate = (double)pr.N * (n_it + 1) / ms;
-        if (rate > best_rate) {
-            best_rate = rate;
-            best_sw = sw;
+    bool tc = false;
+    for (float sw : kTuneSwitches) {
+        TuneVal v = best;
+        v.sw = sw;
+        const double r = tune_rate(pr, base, v, s, &tc);
+        if (r > best_rate) {
+            best_rate = r;
+            best = v;
         }
     }
-    return best_sw;
+    if (base.dense == KM_DENSE_AUTO && tc) {  // the other engine, when the tensor cores take the shape
+        TuneVal v = best;
+        v.dense = KM_DENSE_FP32;
+        const double r = tune_rate(pr, base, v, s, nullptr);
+        if (r > best_rate) {
+            best_rate = r;
+            best = v;
+        }
+    }
+    for (int g : kTuneGrabs) {
+        if (g == best.grab) continue;
+        TuneVal v = best;
+        v.grab = g;
+        const double r = tune_rate(pr, base, v, s, nullptr);
+        if (r > best_rate) {
+            best_rate = r;
+            best = v;
+        }
+    }
+    return best;
 }
 
 void tune_batch(const kmeans_problem *probs, int n, const kmeans_options &base, const char *cache, cudaStream_t s,
-                std::vector<float> &sw) {
-    std::map<TuneKey, float> table;
+                std::vector<TuneVal> &out) {
+    std::map<TuneKey, TuneVal> table;
     if (FILE *f = fopen(cache, "r")) {
-        int D, lk, ln;
-        float v;
-        while (fscanf(f, "%d %d %d %f", &D, &lk, &ln, &v) == 4) table[{D, lk, ln}] = v;
+        char line[256];
+        while (fgets(line, sizeof(line), f)) {
+            int D, lk, ln, dense = base.dense, grab = 32;
+            float v;
+            const int got = sscanf(line, "%d %d %d %f %d %d", &D, &lk, &ln, &v, &dense, &grab);
+            if (got >= 4) table[{D, lk, ln}] = TuneVal{v, got >= 5 ? dense : base.dense, got >= 6 ? grab : 32};
+        }
         fclose(f);
     }
     std::map<TuneKey, int> rep;  // the bucket's largest problem
@@ -1304,12 +1351,14 @@ void tune_batch(const kmeans_problem *probs, int n, const kmeans_options &base, 
     }
     if (grew) {
         if (FILE *f = fopen(cache, "w")) {
-            for (auto &kv : table) fprintf(f, "%d %d %d %.3f\n", kv.first.D, kv.first.lk, kv.first.ln, kv.second);
+            for (auto &kv : table)
+                fprintf(f, "%d %d %d %.3f %d %d\n", kv.first.D, kv.first.lk, kv.first.ln, kv.second.sw,
+                        kv.second.dense, kv.second.grab);
             fclose(f);
         }
     }
-    sw.resize(n);
-    for (int i = 0; i < n; ++i) sw[i] = table[{probs[i].D, ceil_log2(probs[i].K), ceil_log2(probs[i].N)}];
+    out.resize(n);
+    for (int i = 0; i < n; ++i) out[i] = table[{probs[i].D, ceil_log2(probs[i].K), ceil_log2(probs[i].N)}];
 }
 
 int batch_record(kmeans_batch *b, int max_iter, double tol, bool first) {
@@ -1349,13 +1398,19 @@ KM_API int kmeans_batch_init(kmeans_batch **out, int32_t n_problems, const kmean
     kmeans_batch *b = new kmeans_batch;
     cudaGetDevice(&b->dev);
     b->stream = static_cast<cudaStream_t>(base.stream);
-    std::vector<float> sw(n_problems, base.dense_switch);
-    if (tune_cache && tune_cache[0]) tune_batch(problems, n_problems, base, tune_cache, b->stream, sw);
-    b->sw = sw;
+    std::vector<TuneVal> tv(n_problems, TuneVal{base.dense_switch, base.dense, base.surv_grab});
+    if (tune_cache && tune_cache[0]) tune_batch(problems, n_problems, base, tune_cache, b->stream, tv);
+    for (const TuneVal &v : tv) {
+        b->sw.push_back(v.sw);
+        b->dense.push_back(v.dense);
+        b->grab.push_back(v.grab);
+    }
     for (int i = 0; i < n_problems; ++i) {
         const kmeans_problem &pr = problems[i];
         kmeans_options o = base;
-        o.dense_switch = sw[i];
+        o.dense_switch = tv[i].sw;
+        o.dense = tv[i].dense;
+        o.surv_grab = tv[i].grab;
         kmeans_ctx *c = nullptr;
         int rc = kmeans_init(&c, static_cast<const float *>(pr.X), pr.N, pr.D, pr.K, pr.G, pr.init_centroids, &o);
         if (rc) {
@@ -1438,6 +1493,15 @@ KM_API int kmeans_batch_reset(kmeans_batch *b) {
         int rc = kmeans_reset(b->ctx[i], b->c0[i]);
         if (rc) return batch_err(b, rc, "problem %zu: %s", i, b->ctx[i]->err);
     }
+    return KM_OK;
+}
+
+KM_API int kmeans_batch_get_tuning(const kmeans_batch *b, int32_t i, float *dense_switch, int32_t *dense,
+                                   int32_t *surv_grab) {
+    if (!b || i < 0 || i >= (int32_t)b->ctx.size()) return KM_EINVAL;
+    if (dense_switch) *dense_switch = b->sw[i];
+    if (dense) *dense = b->dense[i];
+    if (surv_grab) *surv_grab = b->grab[i];
     return KM_OK;
 }
 

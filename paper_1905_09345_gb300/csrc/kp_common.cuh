@@ -143,6 +143,7 @@ struct Params {
     float tiny;          // absolute slack for underflow
     int32_t algo;
     float dense_frac;    // survivor fraction above which an iteration runs dense
+    int32_t surv_grab;   // survivor queue entries a warp claims at a time (multiple of 32; 0: 32)
     unsigned long long cond;  // cudaGraphConditionalHandle of the fit loop (0: none)
 };
 

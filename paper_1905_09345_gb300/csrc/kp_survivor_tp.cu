@@ -247,13 +247,20 @@ __global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int res
     unsigned long long c_scanned = 0, c_dist = 0, c_recheck = 0, c_changed = 0;
     const int lane = threadIdx.x & 31;
 
-    // dynamic schedule: each warp takes the next 32 queue entries from a
+    // dynamic schedule: each warp claims the next `grab` queue entries from a
     // global counter (points differ a lot in work; a static split leaves
-    // SMs idle at the end)
+    // SMs idle at the end) and works through them 32 at a time, one per lane
+    const int grab = p.surv_grab > 0 ? p.surv_grab : 32;
+    int claim = 0, claim_end = 0;
     for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&ctrl->surv_next, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
+        if (claim >= claim_end) {
+            int b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&ctrl->surv_next, grab);
+            claim = __shfl_sync(0xffffffffu, b0, 0);
+            claim_end = claim + grab;
+        }
+        const int base = claim;
+        claim += 32;
         if (base >= count) break;
         const int64_t it = (int64_t)base + lane;
         const bool active = it < count;

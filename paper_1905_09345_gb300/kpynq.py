@@ -39,7 +39,7 @@ class kmeans_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("grouping", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p), ("dense", ctypes.c_int32),
                 ("dense_switch", ctypes.c_float), ("dtype", ctypes.c_int32), ("pad0", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("surv_grab", ctypes.c_int32), ("pad1", ctypes.c_int32), ("reserved", ctypes.c_int64 * 3)]
 
 
 class kmeans_problem(ctypes.Structure):
@@ -118,6 +118,9 @@ def lib():
         L.kmeans_batch_get.restype = ctypes.c_int
         L.kmeans_batch_reset.argtypes = [vp]
         L.kmeans_batch_reset.restype = ctypes.c_int
+        L.kmeans_batch_get_tuning.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
+                                              ctypes.POINTER(i32)]
+        L.kmeans_batch_get_tuning.restype = ctypes.c_int
         L.kmeans_batch_get_switch.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.kmeans_batch_get_switch.restype = ctypes.c_int
         L.kmeans_batch_destroy.argtypes = [vp]
@@ -526,6 +529,13 @@ def kmeans_batch_get_switch(b, i: int) -> float:
     return v.value
 
 
+def kmeans_batch_get_tuning(b, i: int):
+    """(switch, dense engine, survivor queue entries per claim) of problem i."""
+    sw, de, gr = ctypes.c_float(), ctypes.c_int32(), ctypes.c_int32()
+    _check_batch(lib().kmeans_batch_get_tuning(b, i, ctypes.byref(sw), ctypes.byref(de), ctypes.byref(gr)), b)
+    return sw.value, de.value, gr.value
+
+
 def kmeans_batch_destroy(b) -> None:
     lib().kmeans_batch_destroy(b)
 
@@ -574,6 +584,10 @@ class KMeansBatch:
 
     def switch(self, i: int) -> float:
         return kmeans_batch_get_switch(self.b, i)
+
+    def tuning(self, i: int):
+        """(switch, dense engine, survivor queue entries per claim) of problem i."""
+        return kmeans_batch_get_tuning(self.b, i)
 
     def close(self):
         if getattr(self, "b", None):

@@ -90,7 +90,8 @@ def test_init_rejects_null_and_bad_options(L):
     with pytest.raises(L.KMeansError) as e:
         L.kmeans_init(16, 10, 4, 2, 1, 16, opt)
     assert e.value.status == L.KM_EINVAL
-    for field, bad in (("dtype", 7), ("dtype", -1), ("pad0", 1)):
+    for field, bad in (("dtype", 7), ("dtype", -1), ("pad0", 1), ("pad1", 1), ("surv_grab", 16),
+                       ("surv_grab", 48), ("surv_grab", 2048), ("surv_grab", -32)):
         opt = L.kmeans_default_options()
         setattr(opt, field, bad)
         with pytest.raises(L.KMeansError) as e:

@@ -91,14 +91,18 @@ def test_batch_tuner_writes_and_reuses_cache(kp, tmp_path):
     b = kp.KMeansBatch(probs, tune_cache=cache)
     assert os.path.exists(cache)
     lines = [ln.split() for ln in open(cache) if ln.strip()]
-    table = {(int(a), int(c), int(d)): float(e) for a, c, d, e in lines}
+    assert all(len(ln) == 6 for ln in lines), lines
+    table = {(int(a), int(c), int(d)): (float(e), int(f), int(g)) for a, c, d, e, f, g in lines}
     for i, w in enumerate(ws):
         N, D = w.X.shape
         K = w.C0.shape[0]
         key = (D, int(np.ceil(np.log2(K))) if K > 1 else 0, int(np.ceil(np.log2(N))))
         assert key in table
-        assert b.switch(i) == pytest.approx(table[key])
-        assert table[key] in (0.5, 0.7, 0.9, 1.0)
+        sw, dense, grab = table[key]
+        assert b.switch(i) == pytest.approx(sw)
+        assert sw in (0.5, 0.7, 0.9, 1.0)
+        assert dense in (kp.KM_DENSE_AUTO, kp.KM_DENSE_FP32) and grab in (32, 64, 128)
+        assert b.tuning(i) == (pytest.approx(sw), dense, grab)
     b.fit(10)
     b.close()
     # a second batch reads the cache instead of tuning again
@@ -119,3 +123,48 @@ def test_batch_rejects_bad_calls(kp):
         b.get(5)
     assert e.value.status == kp.KM_EINVAL
     b.close()
+
+
+@pytest.mark.gpu
+def test_batch_reads_older_cache_lines(kp, tmp_path):
+    """A cache line of the older "D logK logN switch" form is read with the
+    default engine and queue schedule."""
+    probs, ws = _problems(n=3, seed0=800)
+    cache = tmp_path / "old.txt"
+    keys = {(w.X.shape[1], int(np.ceil(np.log2(w.C0.shape[0]))) if w.C0.shape[0] > 1 else 0,
+             int(np.ceil(np.log2(w.X.shape[0])))) for w in ws}
+    cache.write_text("".join(f"{d} {k} {n} 0.900\n" for d, k, n in sorted(keys)))
+    b = kp.KMeansBatch(probs, tune_cache=str(cache))
+    for i in range(len(ws)):
+        assert b.tuning(i) == (pytest.approx(0.9), kp.KM_DENSE_AUTO, 32)
+    b.fit(8)
+    for i, w in enumerate(ws):
+        lab = torch.empty(w.X.shape[0], dtype=torch.int32, device="cuda")
+        C = torch.empty(w.C0.shape, device="cuda")
+        J, _ = b.get(i, lab, C)
+        _final_check(w, lab.cpu().numpy(), C.cpu().numpy(), J)
+    b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("grab", [64, 128])
+def test_survivor_queue_schedule_keeps_labels(kp, grab):
+    """A larger survivor queue claim per warp changes only the schedule: the
+    fit equals the default one label for label."""
+    w = synth.anisotropic_1m(N=1 << 15, seed=4)
+    X, C0 = torch.from_numpy(w.X).cuda(), torch.from_numpy(w.C0).cuda()
+    out = []
+    for g in (0, grab):
+        opt = kp.kmeans_default_options()
+        opt.surv_grab = g
+        opt.dense_switch = 1.0
+        ctx = kp.kmeans_init(X, w.N, w.D, w.K, w.G, C0, opt)
+        lab = torch.empty(w.N, dtype=torch.int32, device="cuda")
+        n_iter, J = kp.kmeans_fit(ctx, 12, 0.0, lab)
+        st = [kp.kmeans_get_stats(ctx, t) for t in range(n_iter)]
+        kp.kmeans_destroy(ctx)
+        out.append((lab.cpu().numpy(), n_iter, J, [s["n_dist"] for s in st]))
+    # the cluster sums take their FP64 atomic additions in another order, so
+    # the objective may differ in the last bits; labels and iterations may not
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    assert abs(out[0][2] - out[1][2]) <= 1e-9 * out[0][2]
