@@ -758,6 +758,9 @@ def batched_record(args, dev, seed0=0, steps=None, warmup=None) -> dict:
     units = sum(w.X.shape[0] * it for w, it in zip(works, iters))
     ms = statistics.mean(times)
     switches = sorted(set(round(b.switch(i), 2) for i in range(len(works))))
+    tunings = [b.tuning(i) for i in range(len(works))]
+    tuned = {"problems_on_fp32_engine": sum(1 for t in tunings if t[1] == kpynq.KM_DENSE_FP32),
+             "survivor_claim": {str(g): sum(1 for t in tunings if t[2] == g) for g in sorted({t[2] for t in tunings})}}
     b.close()
     # batched plain Lloyd: the same problems, every distance every iteration
     bl = kpynq.KMeansBatch(probs, stream=stream, algo=kpynq.KM_ALGO_LLOYD)
@@ -795,6 +798,7 @@ def batched_record(args, dev, seed0=0, steps=None, warmup=None) -> dict:
                    "step": "kmeans_batch_reset + kmeans_batch_fit (one graph launch)",
                    "l2": "flushed between steps (256 MiB write)"},
         "clocks": clk.summary(), "init_s": init_s, "generate_s": gen_s, "tuned_switches": switches,
+        "tuned": tuned,
         "batched_plain_lloyd": {"value": lvalue, "ms_per_step": statistics.mean(ltimes)},
         "vs_batched_plain_lloyd": value / lvalue,
         "sequential_single_contexts": {"value": seq_value, "s_per_step": statistics.mean(seq)},
