@@ -82,9 +82,9 @@ enum {
     KM_GROUP_CONTIGUOUS = 0, /* centroid j -> group floor(j * G / K) */
     KM_GROUP_CLUSTERED = 1   /* groups of nearby centroids: plain Lloyd over the K
                                 initial centroids, seeded by their first G rows, 5
-                                iterations (the library's own kernels); a centroid
-                                joins the group of its nearest centre (lowest index
-                                on ties).  Groups left empty are dropped, so fewer
+                                iterations (FP32, on the device); a centroid joins
+                                the group of its nearest centre (lowest index on
+                                ties).  Groups left empty are dropped, so fewer
                                 than G groups may result; bound rows (kmeans_get_bounds)
                                 then hold the remaining groups in the order of
                                 their seeds.  Labels and centroids are always in

@@ -302,7 +302,7 @@ cudaError_t centroids_in(kmeans_ctx *c, const float *src) {
     float *tmp = nullptr;
     cudaError_t e = cudaSuccess;
     if (!is_device_ptr(src)) {
-        e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)p.K * p.D * 4, s);
+        e = pool_alloc(c->dev, reinterpret_cast<void **>(&tmp), (size_t)p.K * p.D * 4, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, src, (size_t)p.K * p.D * 4, cudaMemcpyDefault, s);
         d = tmp;
     }
@@ -318,7 +318,7 @@ cudaError_t centroids_out(kmeans_ctx *c, float *dst, cudaStream_t s) {
     const bool dev = is_device_ptr(dst);
     float *out = dst;
     cudaError_t e = cudaSuccess;
-    if (!dev) e = cudaMallocAsync(reinterpret_cast<void **>(&out), (size_t)p.K * p.D * 4, s);
+    if (!dev) e = pool_alloc(c->dev, reinterpret_cast<void **>(&out), (size_t)p.K * p.D * 4, s);
     if (e == cudaSuccess) e = launch_rows_out(p.C, p.Dp, p.D, p.K, p.orig, out, s, c->num_sms);
     if (!dev && e == cudaSuccess) e = cudaMemcpyAsync(dst, out, (size_t)p.K * p.D * 4, cudaMemcpyDeviceToHost, s);
     if (!dev && out) cudaFreeAsync(out, s);
@@ -330,7 +330,7 @@ cudaError_t labels_out(kmeans_ctx *c, int32_t *dst, cudaStream_t s) {
     const bool dev = is_device_ptr(dst);
     int32_t *out = dst;
     cudaError_t e = cudaSuccess;
-    if (!dev) e = cudaMallocAsync(reinterpret_cast<void **>(&out), (size_t)p.N * 4, s);
+    if (!dev) e = pool_alloc(c->dev, reinterpret_cast<void **>(&out), (size_t)p.N * 4, s);
     if (e == cudaSuccess) e = launch_labels_out(p.label, p.N, p.orig, p.K, out, s, c->num_sms);
     if (!dev && e == cudaSuccess) e = cudaMemcpyAsync(dst, out, (size_t)p.N * 4, cudaMemcpyDeviceToHost, s);
     if (!dev && out) cudaFreeAsync(out, s);
@@ -541,6 +541,13 @@ int check_ctx(kmeans_ctx *c) {
 
 }  // namespace
 
+cudaError_t kp::pool_alloc(int dev, void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    cudaError_t e = lib_pool(dev, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 1), pool, s);
+}
+
 extern "C" {
 
 KM_API void kmeans_default_options(kmeans_options *opt) {
@@ -602,29 +609,29 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     INIT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     INIT_CUDA(cudaMallocHost(&c->ctrl_host, sizeof(Ctrl)));
 
-    // clustered grouping: plain Lloyd over the K initial centroids (this
-    // library's own kernels, an inner context), seeded by their first G rows,
-    // 5 iterations; empty groups are dropped and the centroids are ordered
-    // group by group (ascending caller index within a group), so that every
-    // kernel sees each group as a run of indices.  Ties between equal
-    // distances are broken by the caller's index (Params::orig).
+    // clustered grouping: plain Lloyd over the K initial centroids, seeded by
+    // their first G rows, 5 iterations (kp_group.cu); empty groups are
+    // dropped and the centroids are ordered group by group (ascending caller
+    // index within a group), so that every kernel sees each group as a run
+    // of indices.  Ties between equal distances are broken by the caller's
+    // index (Params::orig).
     std::vector<int32_t> cl_orig, cl_grp, cl_start;
     if (o.grouping == KM_GROUP_CLUSTERED) {
-        kmeans_options go;
-        kmeans_default_options(&go);
-        go.algo = KM_ALGO_LLOYD;
-        go.stream = o.stream;
-        kmeans_ctx *gc = nullptr;
-        rc = kmeans_init(&gc, init_centroids, K, D, G, 1, init_centroids, &go);
-        if (rc) {
-            set_err(c, rc, "grouping: %s", g_init_error);
-            return fail(rc);
-        }
+        cudaStream_t s0 = c->stream;
+        float *cd = nullptr;
+        float *cen = nullptr;
+        int32_t *gd = nullptr;
         std::vector<int32_t> lab(K);
-        rc = kmeans_fit(gc, 5, 0.0, lab.data(), nullptr, nullptr, nullptr);
-        if (rc) set_err(c, rc, "grouping: %s", kmeans_last_error(gc));
-        kmeans_destroy(gc);
-        if (rc) return fail(rc);
+        cudaError_t e = pool_alloc(c->dev, reinterpret_cast<void **>(&cd), (size_t)K * D * 4, s0);
+        if (e == cudaSuccess) e = pool_alloc(c->dev, reinterpret_cast<void **>(&cen), (size_t)G * D * 4, s0);
+        if (e == cudaSuccess) e = pool_alloc(c->dev, reinterpret_cast<void **>(&gd), (size_t)K * 4, s0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cd, init_centroids, (size_t)K * D * 4, cudaMemcpyDefault, s0);
+        if (e == cudaSuccess) e = launch_clustered_groups(cd, K, D, G, 5, gd, cen, s0, c->num_sms);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lab.data(), gd, (size_t)K * 4, cudaMemcpyDeviceToHost, s0);
+        for (void *q : {(void *)cd, (void *)cen, (void *)gd})
+            if (q) cudaFreeAsync(q, s0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+        INIT_CUDA(e);
         std::vector<int32_t> cnt(G, 0), newid(G, -1);
         for (int k = 0; k < K; ++k) {
             if ((unsigned)lab[k] >= (unsigned)G) {
@@ -670,7 +677,7 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         const uint16_t *xb = reinterpret_cast<const uint16_t *>(X);
         uint16_t *tmp = nullptr;
         if (!is_device_ptr(X)) {
-            INIT_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)N * D * 2, c->stream));
+            INIT_CUDA(pool_alloc(c->dev, reinterpret_cast<void **>(&tmp), (size_t)N * D * 2, c->stream));
             INIT_CUDA(cudaMemcpyAsync(tmp, X, (size_t)N * D * 2, cudaMemcpyDefault, c->stream));
             xb = tmp;
         }
@@ -1026,7 +1033,7 @@ KM_API int kmeans_get_bounds(kmeans_ctx *c, float *u, float *lbg, float *lb) {
     for (int i = 0; i < 3; ++i) {
         if (!outs[i]) continue;
         if (is_device_ptr(outs[i])) dev[i] = outs[i];
-        else KP_CUDA(c, cudaMallocAsync(&dev[i], sizes[i] * 4, c->stream));
+        else KP_CUDA(c, pool_alloc(c->dev, reinterpret_cast<void **>(&dev[i]), sizes[i] * 4, c->stream));
     }
     KP_CUDA(c, launch_bounds_out(p, c->stream, dev[0], dev[1], dev[2], c->num_sms));
     for (int i = 0; i < 3; ++i) {

@@ -400,6 +400,16 @@ cudaError_t launch_kmeanspp(const float *X, int64_t N, int D, int K, const doubl
                             double *dmin, unsigned long long *bsum, void *state, cudaStream_t s, int num_sms,
                             long long *err_out);
 size_t kmeanspp_state_bytes();
+// stream-ordered allocation from the library's own pool on `dev` (it keeps
+// freed memory mapped across synchronisations, unlike the default pool with
+// its zero release threshold); free with cudaFreeAsync
+cudaError_t pool_alloc(int dev, void **p, size_t bytes, cudaStream_t s);
+
+// clustered grouping (kp_group.cu): grp[K] from C (K x D, dense rows), G
+// centres seeded by the first G rows, `iters` Lloyd iterations; cen (G x D
+// floats) is scratch
+cudaError_t launch_clustered_groups(const float *C, int K, int D, int G, int iters, int32_t *grp, float *cen,
+                                    cudaStream_t s, int num_sms);
 // the caller's centroid numbering (kp_update.cu)
 cudaError_t launch_labels_out(const int32_t *label, int64_t N, const int32_t *orig, int K, int32_t *out,
                               cudaStream_t s, int num_sms);

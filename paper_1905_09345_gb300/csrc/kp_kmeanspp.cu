@@ -260,12 +260,12 @@ KM_API int kmeans_init_kmeanspp(const float *X, int64_t N, int32_t D, int32_t K,
     float *Cd = nullptr;
     long long *idx = nullptr;
     long long err = 0;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&dmin), (size_t)N * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&bsum), (size_t)nb * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&st, kmeanspp_state_bytes(), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&ud), (size_t)K * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&Cd), (size_t)K * D * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&idx), (size_t)K * 8, s);
+    cudaError_t e = pool_alloc(dev, reinterpret_cast<void **>(&dmin), (size_t)N * 8, s);
+    if (e == cudaSuccess) e = pool_alloc(dev, reinterpret_cast<void **>(&bsum), (size_t)nb * 8, s);
+    if (e == cudaSuccess) e = pool_alloc(dev, &st, kmeanspp_state_bytes(), s);
+    if (e == cudaSuccess) e = pool_alloc(dev, reinterpret_cast<void **>(&ud), (size_t)K * 8, s);
+    if (e == cudaSuccess) e = pool_alloc(dev, reinterpret_cast<void **>(&Cd), (size_t)K * D * 4, s);
+    if (e == cudaSuccess) e = pool_alloc(dev, reinterpret_cast<void **>(&idx), (size_t)K * 8, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ud, u, (size_t)K * 8, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = launch_kmeanspp(X, N, D, K, ud, Cd, idx, dmin, bsum, st, s, sms, &err);
     if (e == cudaSuccess) e = cudaMemcpyAsync(centroids, Cd, (size_t)K * D * 4, cudaMemcpyDefault, s);

@@ -581,7 +581,7 @@ int mlp_fail(kmeans_mlp *m, int code, const char *fmt, ...) {
 template <class T>
 cudaError_t mlp_alloc(kmeans_mlp *m, T **p, size_t n, std::vector<void *> &list) {
     void *v = nullptr;
-    cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(n, 1) * sizeof(T), m->stream);
+    cudaError_t e = pool_alloc(m->dev, &v, std::max<size_t>(n, 1) * sizeof(T), m->stream);
     if (e != cudaSuccess) return e;
     list.push_back(v);
     *p = static_cast<T *>(v);

@@ -286,17 +286,18 @@ def test_clustered_grouping_lockstep(kp, N, D, K, G, iters, dense):
     lockstep(kp, X, C0, G, iters, grouping=kp.KM_GROUP_CLUSTERED, dense=dense)
 
 
-def test_clustered_grouping_equals_oracle(kp):
+@pytest.mark.parametrize("G,per,D,Gqs", [(10, 12, 8, (1, 4, 10, 30)), (40, 15, 40, (1, 33, 40, 70))])
+def test_clustered_grouping_equals_oracle(kp, G, per, D, Gqs):
     """The library's clustered grouping (Lloyd over the centroids with its own
     kernels) is the oracle's, with empty groups dropped and the rest numbered
     in the order of their seeds; well-separated centroid clouds, so no group
-    assignment is a near-tie."""
+    assignment is a near-tie.  The second case spans several member chunks of
+    the update (K = 600) and more groups than a warp has lanes."""
     rng = np.random.default_rng(12)
-    G, per, D = 10, 12, 8
     clouds = rng.uniform(-50, 50, (G, D))
     C0 = (clouds[rng.permutation(np.repeat(np.arange(G), per))] + rng.normal(0, 0.5, (G * per, D))).astype(np.float32)
     X = np.concatenate([C0, C0 + rng.normal(0, 0.1, C0.shape).astype(np.float32)])
-    for Gq in (1, 4, 10, 30):
+    for Gq in Gqs:
         km = kp.KMeans(dev(X), dev(C0), Gq, grouping=kp.KM_GROUP_CLUSTERED)
         grp = np.empty(C0.shape[0], np.int32)
         ng = km.groups(grp)
