@@ -825,14 +825,17 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     if (c->use_tc) {  // the two bfloat16 halves of X, made once
         uint16_t *xh, *xl;
         const int Dt = tc_dim(D);  // zero-padded width of the operand copies
+        float *xnorm;
         INIT_CUDA(dalloc(c, &xh, (size_t)N * Dt));
         INIT_CUDA(dalloc(c, &xl, (size_t)N * Dt));
+        INIT_CUDA(dalloc(c, &xnorm, (size_t)N));
         // from the host copy when X is still there (the FP32 copy is made in the same pass)
         INIT_CUDA(launch_split_x(x_host_dev ? x_host_dev : p.X, N, D, Dt, xh, xl, s, c->num_sms,
-                                 x_host_dev ? c->X_own : nullptr, p.mu));
+                                 x_host_dev ? c->X_own : nullptr, p.mu, xnorm));
         x_host_dev = nullptr;
         p.Xh = xh;
         p.Xl = xl;
+        p.xnorm = xnorm;
         SettleReq *sq;
         INIT_CUDA(dalloc(c, &sq, (size_t)N));
         p.sreq = sq;

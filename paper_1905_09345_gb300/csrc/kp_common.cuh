@@ -84,6 +84,7 @@ struct Params {
     const float *X;      // N x D, row-major
     const uint16_t *Xh;  // N x D bfloat16: bf16(x)            (tensor-core path)
     const uint16_t *Xl;  // N x D bfloat16: bf16(x - bf16(x))  (tensor-core path)
+    const float *xnorm;  // N: ||x - mu||^2 of the values split into Xh / Xl, FP32 (tensor-core path)
     int64_t N;
     int32_t D, K, G;
     int32_t Dp;          // centroid row stride (floats), >= D, multiple of 4
@@ -374,7 +375,7 @@ int dense_tcb_kp(const Params &p);  // padded K of the split centroid copy
 cudaError_t launch_dense_tcb(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                              size_t smem_limit, int if_dense);
 cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
-                           int num_sms, float *Xcopy = nullptr, const float *mu = nullptr);
+                           int num_sms, float *Xcopy = nullptr, const float *mu = nullptr, float *xnorm = nullptr);
 cudaError_t launch_dense_tc(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms,
                             size_t smem_limit, int if_dense = 0);
 cudaError_t launch_settle(const Params &p, cudaStream_t s, int first, int respect_done, int num_sms);

@@ -67,7 +67,7 @@ struct TcCfg {
     int num_tiles;
     float e_lin;   // 1.25 (6.1 2^-16 + (6D+1) 2^-23), rounded up
     float e_c2;    // 1.25 (D+3) 2^-24, rounded up
-    float xn_lo, xn_hi;  // relative error of ||x||^2 from the split copy
+    float xn_lo, xn_hi;  // relative error of the precomputed ||x - mu||^2
 };
 
 template <int D>
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             bar_init(&full_a[i], 1);
-            bar_init(&empty_a[i], kEpiWarps / 2);  // the warps that read the row norms
+            bar_init(&empty_a[i], 1);  // the commit of the MMAs that read the stage
         }
         for (int g = 0; g < kGroups; ++g) {
             bar_init(&acc_full[g], 1);
@@ -241,6 +241,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         "l"(dah), "l"(dbh), "r"(idesc), "r"(acc), "l"(dbl), "l"(dal)
                         : "memory");
                 }
+                // the A stage is free once these MMAs have read it
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty_a[s]))
+                             : "memory");
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&acc_full[buf]))
                              : "memory");
@@ -278,12 +282,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int i = grp_id;
         for (int tile = blockIdx.x + grp_id * gridDim.x; tile < cfg.num_tiles;
              tile += kGroups * gridDim.x, i += kGroups) {
-            const int s = i % S, f = i / S;
             const int u = i / kGroups;
             // waits are warp-uniform (the TMEM loads below are warp-collective)
             // and pair-uniform (the named barriers need both warps)
-            bool ok = __all_sync(0xffffffffu, bar_wait(&acc_full[grp_id], u & 1, ctrl));
-            if (half == 0) ok = ok && __all_sync(0xffffffffu, bar_wait(&full_a[s], f & 1, ctrl));
+            const bool ok = __all_sync(0xffffffffu, bar_wait(&acc_full[grp_id], u & 1, ctrl));
             if (!pair_and(ok, pid)) break;
             tc_fence_after();
             const int64_t n = (int64_t)tile * kTM + r;
@@ -293,11 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (half == 0) {
                 // the previous label, read now so that its latency hides behind the scan
                 old = valid ? (first ? -1 : p.label[n]) : -1;
-                const uint8_t *st = sA + (size_t)s * 2 * NA * kAtomBytes;
-                const float xn = row_norm2<D>(st, st + NA * kAtomBytes, r);
-                // the split copy of A is no longer needed
-                __syncwarp();
-                if (lane == 0) bar_arrive(&empty_a[s]);
+                const float xn = valid ? p.xnorm[n] : 0.f;
                 xlo = __fmul_rd(xn, cfg.xn_lo);
                 xup = __fmul_ru(xn, cfg.xn_hi);
                 E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
@@ -496,30 +494,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // X -> (x_h, x_l) bfloat16 copies with rows of Dt >= D coordinates (zero
-// padding), four elements per thread
+// padding), four elements per thread, and each row's ||x - mu||^2 (FP32 sum of
+// the squares of the values split, reduced over the Dt / 4 lanes of the row).
+// Dt / 4 is 16 or 32 and the loop steps by whole warps, so a row's lanes are
+// one aligned half-warp or warp and all of them run every iteration.
 __global__ void k_split_x(const float *X, int64_t N, int D, int Dt, uint2 *Xh, uint2 *Xl, float4 *Xcopy,
-                          const float *mu) {
+                          const float *mu, float *xnorm) {
     const int q4n = Dt / 4;
     const int64_t n4 = N * q4n;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n4; base += stride) {
+        const int64_t i = base + lane;
+        const bool act = i < n4;
         const int64_t row = i / q4n;
         const int q4 = (int)(i - row * q4n);
-        const float4 a = q4 * 4 < D ? *reinterpret_cast<const float4 *>(X + row * D + q4 * 4) : make_float4(0, 0, 0, 0);
-        if (Xcopy && q4 * 4 < D) Xcopy[(row * D + q4 * 4) / 4] = a;  // the device copy, in the same pass
-        // x - mu, rounded once to FP32 (the padding stays exactly zero)
-        const float4 m = (mu && q4 * 4 < D) ? *reinterpret_cast<const float4 *>(mu + q4 * 4) : make_float4(0, 0, 0, 0);
-        const float vv[4] = {__fsub_rn(a.x, m.x), __fsub_rn(a.y, m.y), __fsub_rn(a.z, m.z), __fsub_rn(a.w, m.w)};
-        uint32_t hw[2], lw[2];
+        float ss = 0.f;
+        if (act) {
+            const float4 a =
+                q4 * 4 < D ? *reinterpret_cast<const float4 *>(X + row * D + q4 * 4) : make_float4(0, 0, 0, 0);
+            if (Xcopy && q4 * 4 < D) Xcopy[(row * D + q4 * 4) / 4] = a;  // the device copy, in the same pass
+            // x - mu, rounded once to FP32 (the padding stays exactly zero)
+            const float4 m =
+                (mu && q4 * 4 < D) ? *reinterpret_cast<const float4 *>(mu + q4 * 4) : make_float4(0, 0, 0, 0);
+            const float vv[4] = {__fsub_rn(a.x, m.x), __fsub_rn(a.y, m.y), __fsub_rn(a.z, m.z), __fsub_rn(a.w, m.w)};
+            uint32_t hw[2], lw[2];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            __nv_bfloat16 h0 = __float2bfloat16_rn(vv[2 * k]), h1 = __float2bfloat16_rn(vv[2 * k + 1]);
-            __nv_bfloat16 l0 = __float2bfloat16_rn(vv[2 * k] - __bfloat162float(h0));
-            __nv_bfloat16 l1 = __float2bfloat16_rn(vv[2 * k + 1] - __bfloat162float(h1));
-            hw[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            lw[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            for (int k = 0; k < 2; ++k) {
+                __nv_bfloat16 h0 = __float2bfloat16_rn(vv[2 * k]), h1 = __float2bfloat16_rn(vv[2 * k + 1]);
+                __nv_bfloat16 l0 = __float2bfloat16_rn(vv[2 * k] - __bfloat162float(h0));
+                __nv_bfloat16 l1 = __float2bfloat16_rn(vv[2 * k + 1] - __bfloat162float(h1));
+                hw[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                lw[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            Xh[i] = make_uint2(hw[0], hw[1]);
+            Xl[i] = make_uint2(lw[0], lw[1]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ss = fmaf(vv[k], vv[k], ss);
         }
-        Xh[i] = make_uint2(hw[0], hw[1]);
-        Xl[i] = make_uint2(lw[0], lw[1]);
+        for (int o = q4n >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (act && q4 == 0 && xnorm) xnorm[row] = ss;
     }
 }
 
@@ -563,8 +577,10 @@ bool plan(const Params &p, size_t smem_limit, TcCfg &cfg, size_t &smem) {
     const double D = Dt;  // the padded width: its zero products add nothing, the bound stays valid
     cfg.e_lin = (float)(1.25 * (6.1 * std::ldexp(1.0, -16) + (6 * D + 1) * std::ldexp(1.0, -23)) * (1 + 1e-6));
     cfg.e_c2 = (float)(1.25 * (D + 3) * std::ldexp(1.0, -24) * (1 + 1e-6));
-    // ||x||^2 from x_h + x_l: (1 +- 2^-16)^2 per element and an FP32 sum of D squares
-    const double rel = 2 * (std::ldexp(1.0, -15) + (D + 2) * std::ldexp(1.0, -24));
+    // ||x - mu||^2 from k_split_x: an FP32 sum of non-negative terms in which
+    // each term meets at most 4 + log2(Dt / 4) <= 9 roundings, so the relative
+    // error is below 9.01 2^-24 < 2^-20
+    const double rel = std::ldexp(1.0, -20);
     cfg.xn_lo = (float)(1.0 - rel);
     cfg.xn_hi = (float)(1.0 + rel);
     return true;
@@ -575,7 +591,7 @@ cudaError_t launch_t(const Params &p, cudaStream_t s, int first, int respect_don
                      int if_dense) {
     TcCfg cfg;
     size_t smem;
-    if (!plan(p, smem_limit, cfg, smem) || !p.Xh || !p.Xl) return cudaErrorNotSupported;
+    if (!plan(p, smem_limit, cfg, smem) || !p.Xh || !p.Xl || !p.xnorm) return cudaErrorNotSupported;
     auto enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tmh, tml;
@@ -607,13 +623,14 @@ bool dense_tc_eligible(const Params &p, size_t smem_limit) {
 }
 
 cudaError_t launch_split_x(const float *X, int64_t N, int D, int Dt, uint16_t *Xh, uint16_t *Xl, cudaStream_t s,
-                           int num_sms, float *Xcopy, const float *mu) {
+                           int num_sms, float *Xcopy, const float *mu, float *xnorm) {
+    if (Dt != 64 && Dt != 128) return cudaErrorInvalidValue;  // a row's lanes: one half-warp or warp
     const int64_t n4 = N * Dt / 4;  // D and Dt are multiples of 4
     const int64_t grid = std::min<int64_t>((n4 + 255) / 256, (int64_t)num_sms * 16);
     count_launch();
     k_split_x<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(X, N, D, Dt, reinterpret_cast<uint2 *>(Xh),
                                                                     reinterpret_cast<uint2 *>(Xl),
-                                                                    reinterpret_cast<float4 *>(Xcopy), mu);
+                                                                    reinterpret_cast<float4 *>(Xcopy), mu, xnorm);
     return cudaGetLastError();
 }
 

@@ -100,29 +100,6 @@ __device__ __forceinline__ void split8(const float *v, uint4 &h, uint4 &l) {
     h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
-__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-
-// ||x||^2 of one row of the split A tile, from x_h + x_l
-template <int D>
-__device__ __forceinline__ float row_norm2(const uint8_t *Ah, const uint8_t *Al, int row) {
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < D / 8; ++q) {
-        const uint4 h = *reinterpret_cast<const uint4 *>(Ah + swz_chunk(row, q, kAtomBytes));
-        const uint4 l = *reinterpret_cast<const uint4 *>(Al + swz_chunk(row, q, kAtomBytes));
-        const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float v0 = bf_lo(hw[i]) + bf_lo(lw[i]);
-            const float v1 = bf_hi(hw[i]) + bf_hi(lw[i]);
-            a0 = fmaf(v0, v0, a0);
-            a1 = fmaf(v1, v1, a1);
-        }
-    }
-    return a0 + a1;
-}
-
 // Running scan of one row over a run of accumulator columns: the per-group
 // minima (stored into the row's shared-memory slots as each group closes),
 // and the smallest value with its index and the runner-up, in two independent
