@@ -279,6 +279,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int k0 = half ? ha : 0, k1 = half ? nch : ha;
         const int gsplit = nch > 1 ? group_of(bm, 32 * ha - 1) : 0;
         unsigned long long c_changed = 0, c_recheck = 0, c_dist = 0;
+        auto write_req = [&](int64_t n, int old, int i1, float xlo, float b1, float E, unsigned long long gmask) {
+            SettleReq rq;
+            rq.n = (int32_t)n;
+            rq.old = old;
+            rq.i1 = i1;
+            // every column is at least b1: when i1 loses, this bounds both i1's
+            // group (which now keeps i1) and the winner's group
+            rq.lb_alt = sqrt_lo(__fsub_rd(__fadd_rd(xlo, b1), E));
+            rq.gmask = gmask;
+            rq.lim = 0.f;
+            p.sreq[n] = rq;
+        };
+        // the lb-row store: this lane's first float4 of a 16-row block and the
+        // step of 32 float4s, as (row, column) pairs
+        const int st_q4 = p.Gp >> 2;
+        const int st_r0 = lane / st_q4, st_g0 = lane - st_r0 * st_q4;
+        const int st_dr = 32 / st_q4, st_dg = 32 - st_dr * st_q4;
         int i = grp_id;
         for (int tile = blockIdx.x + grp_id * gridDim.x; tile < cfg.num_tiles;
              tile += kGroups * gridDim.x, i += kGroups) {
@@ -292,6 +309,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool valid = n < p.N;
             int old = -1;
             float xlo = 0.f, xup = 0.f, E = 0.f;
+            bool need_row = false;  // half 0: this row's settle request, written after the conversion
+            int best_row = 0;
+            float b1_row = 0.f;
             if (half == 0) {
                 // the previous label, read now so that its latency hides behind the scan
                 old = valid ? (first ? -1 : p.label[n]) : -1;
@@ -367,28 +387,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // such a row's bounds as if the tensor-core winner i1 won; k_settle
                 // corrects them when it does not.
                 const bool need = valid && b2 <= thr;
+                need_row = bounds && need;
+                best_row = i1;
+                b1_row = b1;
                 {
                     const unsigned nm = __ballot_sync(0xffffffffu, need);
-                    if (nm) {
-                        // the groups that can hold a window column: group minimum
-                        // within the window (at most 64 groups; more: all of them)
+                    // The groups that can hold a window column: group minimum
+                    // within the window (at most 64 groups; more: all of them).
+                    // With bounds, the pair tests its halves of the groups while
+                    // converting them, and half 0 writes the request afterwards.
+                    if (nm && !bounds) {
                         unsigned long long gmask = ~0ull;
                         if (G <= 64) {
                             gmask = 0ull;
                             for (int g = 0; g < G; ++g) gmask |= (row[g] <= thr) ? (1ull << g) : 0ull;
                         }
-                        if (need) {
-                            SettleReq rq;
-                            rq.n = (int32_t)n;
-                            rq.old = old;
-                            rq.i1 = i1;
-                            // every column is at least b1: when i1 loses, this bounds both
-                            // i1's group (which now keeps i1) and the winner's group
-                            rq.lb_alt = sqrt_lo(__fsub_rd(__fadd_rd(xlo, b1), E));
-                            rq.gmask = gmask;
-                            rq.lim = 0.f;
-                            p.sreq[n] = rq;
-                        }
+                        if (need) write_req(n, old, i1, xlo, b1, E, gmask);
                     }
                     // the warp's 32 rows in the request bitmap (every word is written
                     // by every dense pass, so the bitmap needs no clearing)
@@ -414,7 +428,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         p.stamp[n] = make_stamp(v, v);
                     }
                 }
-                *mrow = make_float4(xlo, E, 0.f, 0.f);  // for half 1's share of the conversion
+                *mrow = make_float4(xlo, E, thr, 0.f);  // for half 1's share of the conversion
                 {
                     // label changes: one slot reservation per warp
                     const bool moved = valid && !need && old != best;
@@ -436,17 +450,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (bounds) {
                 // s_c >= xn_lo + t_c - E for every column c: the pair converts the
                 // row's group minima, half 0 the first half of the groups
+                // and each half marks its groups whose minimum is within the
+                // window (bit g - g0; the winner's group holds tw = b2 <= thr)
                 const int gh = (G + 1) >> 1;
+                uint32_t gbits = 0u;
                 if (valid) {
                     const float4 xe = *mrow;
                     const int g0 = half ? gh : 0, g1 = half ? G : gh;
+                    if (G <= 64) {  // gh <= 32: one 32-bit word per half
 #pragma unroll 4
-                    for (int g = g0; g < g1; ++g) {
-                        const float tg = row[g];
-                        row[g] = tg == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xe.x, tg), xe.y));
+                        for (int g = g0; g < g1; ++g) {
+                            const float tg = row[g];
+                            gbits |= (tg <= xe.z ? 1u : 0u) << (g - g0);
+                            row[g] = tg == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xe.x, tg), xe.y));
+                        }
+                    } else {
+#pragma unroll 4
+                        for (int g = g0; g < g1; ++g) {
+                            const float tg = row[g];
+                            row[g] = tg == INFINITY ? INFINITY : sqrt_lo(__fsub_rd(__fadd_rd(xe.x, tg), xe.y));
+                        }
                     }
+                    if (half) row[p.Gp] = __uint_as_float(gbits);  // the slot past the groups
                 }
-                pair_sync(pid);  // the rows' bounds are complete
+                pair_sync(pid);  // the rows' bounds and half 1's group bits are complete
+                if (half == 0 && need_row) {
+                    const unsigned long long gmask =
+                        G <= 64 ? ((unsigned long long)gbits | ((unsigned long long)__float_as_uint(row[p.Gp]) << gh))
+                                : ~0ull;
+                    write_req(n, old, best_row, xlo, b1_row, E, gmask);
+                }
                 // the quadrant's 32 rows (consecutive points) as one contiguous
                 // block, half 0 the first 16 rows, half 1 the rest
                 const int64_t n0 = (int64_t)tile * kTM + q * 32;
@@ -454,19 +487,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int r0 = half * 16, r1 = min(rows, r0 + 16);
                 if (r1 > r0) {
                     // rows x Gp floats, contiguous in lb: 16-byte stores (Gp is a
-                    // multiple of 4, so no vector crosses a row)
-                    const int Gp = p.Gp, q4 = Gp >> 2;
+                    // multiple of 4, so no vector crosses a row); lane-strided
+                    // element e = rw * q4 + gq, (rw, gq) stepped without division
+                    const int Gp = p.Gp;
                     const float *st0 = stage + (size_t)(grp_id * kTM + q * 32) * (Gp + 1);
                     float4 *dst = reinterpret_cast<float4 *>(p.lb + n0 * Gp);
-                    for (int ee = r0 * q4 + lane; ee < r1 * q4; ee += 32) {
-                        const int rw = ee / q4, g = (ee - rw * q4) * 4;
+                    for (int rw = r0 + st_r0, gq = st_g0; rw < r1;) {
+                        const int g = gq * 4;
                         const float *src = st0 + rw * (Gp + 1) + g;
                         float4 v4;
                         v4.x = g < G ? src[0] : 0.f;
                         v4.y = g + 1 < G ? src[1] : 0.f;
                         v4.z = g + 2 < G ? src[2] : 0.f;
                         v4.w = g + 3 < G ? src[3] : 0.f;
-                        dst[ee] = v4;
+                        dst[rw * st_q4 + gq] = v4;
+                        rw += st_dr;
+                        gq += st_dg;
+                        if (gq >= st_q4) {
+                            gq -= st_q4;
+                            ++rw;
+                        }
                     }
                 }
             }
