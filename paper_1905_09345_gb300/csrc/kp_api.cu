@@ -338,15 +338,14 @@ cudaError_t labels_out(kmeans_ctx *c, int32_t *dst, cudaStream_t s) {
 }
 
 // One assignment (dense when `dense`, filtered otherwise), stream-ordered.
-// Cluster statistics after an assignment: the full recompute (when the device
-// chooses it) and the incremental moves (otherwise).
+// Cluster statistics after an assignment: the full recompute or the moved
+// points' changes, chosen on the device.
 cudaError_t enqueue_stats(kmeans_ctx *c, const Params &p, cudaStream_t s, int all_points, int respect_done) {
     const int n = c->num_sms;
-    if (stats_full_supported(p)) {
-        cudaError_t e = timed(c, s, KM_KERNEL_STATS, [&] { return launch_stats_full(p, s, all_points, respect_done, n); });
-        if (e != cudaSuccess) return e;
-        all_points = 0;  // the full recompute covers iteration 0
-    }
+    // the sorted path takes both modes (full recompute or moved points only,
+    // chosen on the device); the per-point moves are for the other layouts
+    if (stats_full_supported(p))
+        return timed(c, s, KM_KERNEL_STATS, [&] { return launch_stats_full(p, s, all_points, respect_done, n); });
     return timed(c, s, KM_KERNEL_MOVES, [&] { return launch_apply_moves(p, s, all_points, respect_done, n); });
 }
 
