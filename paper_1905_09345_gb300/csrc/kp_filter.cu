@@ -543,8 +543,10 @@ __global__ void __launch_bounds__(512, 2) k_survivor(Params p, int respect_done,
 }
 
 cudaError_t launch_filter(const Params &p, cudaStream_t s, int respect_done, int num_sms) {
+    // two blocks per SM: each block adds its bucket counts to the global ones
+    // (and reserves queue ranges), so fewer blocks mean fewer contended atomics
     int64_t warps = (p.N + 127) / 128;
-    int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms * 8);
+    int64_t grid = std::min<int64_t>((warps + 7) / 8, (int64_t)num_sms * 2);
     grid = std::max<int64_t>(grid, 1);
     const size_t smem1 = (size_t)p.nbucket * 4, smem2 = 2 * smem1;
     cudaError_t e = cudaFuncSetAttribute(k_filter_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);

@@ -70,8 +70,14 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_hist(Params p, int all_
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->stats_full = full ? 1 : 0;
     const int K = p.K, D = p.D;
     const bool local = K <= p.hist_smem_k;
+    const int64_t m = full ? 0 : (int64_t)ctrl->moved_count;
+    const int64_t ne = stats_entries(p, full);
+    // blocks taking part: one per tile of entries (the others leave at once;
+    // few moved points need few blocks)
+    const unsigned used = (unsigned)max((int64_t)1, min((int64_t)gridDim.x, (ne + kStatsTile - 1) / kStatsTile));
+    if (blockIdx.x >= used) return;
     const int64_t tid = (int64_t)blockIdx.x * kStatsThreads + threadIdx.x;
-    const int64_t nthr = (int64_t)gridDim.x * kStatsThreads;
+    const int64_t nthr = (int64_t)used * kStatsThreads;
     if (full) {
         for (int64_t i = tid; i < (int64_t)K * D; i += nthr) p.S[i] = 0.0;
         for (int64_t i = tid; i < K; i += nthr) p.Q[i] = 0.0;
@@ -84,8 +90,6 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_hist(Params p, int all_
         for (int i = threadIdx.x; i < K; i += kStatsThreads) hist[i] = 0;
         __syncthreads();
     }
-    const int64_t m = full ? 0 : (int64_t)ctrl->moved_count;
-    const int64_t ne = stats_entries(p, full);
     for (int64_t e = tid; e < ne; e += nthr) {
         uint32_t id;
         const int k = stats_entry(p, full, m, e, id);
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_hist(Params p, int all_
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&ctrl->stats_ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->stats_ticket, 1u) == used - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -154,6 +158,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_scatter(Params p, int r
         }
         return;
     }
+    if ((int64_t)blockIdx.x * kStatsTile >= ne) return;  // no tile for this block (block-uniform)
     int *cnt = sh;
     int *base = sh + K;
     for (int i = threadIdx.x; i < K; i += kStatsThreads) cnt[i] = 0;
@@ -316,7 +321,9 @@ cudaError_t launch_stats_full(const Params &p, cudaStream_t s, int all_points, i
         cudaError_t e = cudaFuncSetAttribute(k_stats_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h2);
         if (e != cudaSuccess) return e;
         const int64_t blocks = (p.N + kStatsTile - 1) / kStatsTile;
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms * 8));
+        // two blocks per SM: each block adds its counts to the K global ones
+        // and takes a ticket, so fewer blocks mean fewer contended atomics
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)num_sms * 2));
         count_launch();
         k_stats_hist<<<grid, kStatsThreads, h1, s>>>(p, all_points, respect_done);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
