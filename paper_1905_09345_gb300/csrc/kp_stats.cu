@@ -7,7 +7,7 @@
 // warp sums a run of 64 sorted entries coordinate-parallel and adds one
 // partial per cluster it met to the global FP64 sums.  Global atomics then
 // touch each cluster a few times instead of once per point.
-//   * full recompute (iteration 0, or more than N/16 labels changed): one
+//   * full recompute (iteration 0, or more than N/2 labels changed): one
 //     entry per point, under its label; S, Q and the counts start from zero;
 //   * incremental (few labels changed): two entries per relabelled point,
 //     +x under its new label and -x under its old one (the sign in bit 31 of
@@ -22,8 +22,9 @@ constexpr int kStatsTile = kStatsThreads * 4;  // points per block step of the s
 constexpr int kSumRun = 64;                    // sorted points per warp in k_stats_sum
 constexpr int kSumMaxPer = 8;                  // coordinates per lane (D <= 256)
 
+// full when the moved points' entries (two each) would outnumber the points
 __device__ __forceinline__ bool stats_full_rule(const Params &p, int all_points) {
-    return all_points || (int64_t)p.ctrl->moved_count * 16 > p.N;
+    return all_points || (int64_t)p.ctrl->moved_count * 2 > p.N;
 }
 
 constexpr uint32_t kNegEntry = 0x80000000u;  // entry id bit: subtract the point
