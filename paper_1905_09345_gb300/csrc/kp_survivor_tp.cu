@@ -215,8 +215,10 @@ struct TpLayout {
     }
 };
 
+// two blocks per SM up to 64 coordinates; at 128 the point's registers (64
+// for x alone) leave room for one
 template <int DP, bool STAGE>
-__global__ void __launch_bounds__(kTpThreads, 2) k_survivor_tp(Params p, int respect_done) {
+__global__ void __launch_bounds__(kTpThreads, DP > 64 ? 1 : 2) k_survivor_tp(Params p, int respect_done) {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     Ctrl *ctrl = p.ctrl;
@@ -519,7 +521,7 @@ cudaError_t launch_tp(const Params &p, cudaStream_t s, int respect_done, int num
 
 bool survivor_tp_eligible(const Params &p) {
     const int dp = dense_dp(p.D);
-    return dp > 0 && dp <= 64 && p.K < 0x7fffffff;
+    return dp > 0 && dp <= 128 && p.K < 0x7fffffff;
 }
 
 cudaError_t launch_survivor_tp(const Params &p, cudaStream_t s, int respect_done, int num_sms, size_t smem_limit) {
@@ -530,6 +532,7 @@ cudaError_t launch_survivor_tp(const Params &p, cudaStream_t s, int respect_done
     case 16: return launch_tp<16>(p, s, respect_done, num_sms, smem_limit);
     case 32: return launch_tp<32>(p, s, respect_done, num_sms, smem_limit);
     case 64: return launch_tp<64>(p, s, respect_done, num_sms, smem_limit);
+    case 128: return launch_tp<128>(p, s, respect_done, num_sms, smem_limit);
     default: return cudaErrorInvalidValue;
     }
 }
