@@ -19,7 +19,9 @@ namespace kp {
 
 constexpr int kStatsThreads = 256;
 constexpr int kStatsTile = kStatsThreads * 4;  // points per block step of the scatter
-constexpr int kSumRun = 64;                    // sorted points per warp in k_stats_sum
+constexpr int kSumRun = 64;                    // sorted entries per warp in k_stats_sum (full mode)
+constexpr int kSumRunMoved = 16;               // the same for at most N/8 moved points' entries
+                                               // (few, so shorter runs put more warps on them)
 constexpr int kSumMaxPer = 8;                  // coordinates per lane (D <= 256)
 
 // full when the moved points' entries (two each) would outnumber the points
@@ -201,7 +203,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Each warp sums kSumRun consecutive sorted entries, lanes over the
+// Each warp sums a run of consecutive sorted entries, lanes over the
 // coordinates, eight entries' loads in flight at a time, and adds its partial
 // sums to S and Q (and, in incremental mode, the count change to cnt) whenever
 // the cluster changes along the run (and at its end).  A subtracted entry
@@ -227,8 +229,9 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_sum(Params p, int respe
     // entries placed: the hist kernel's count (entries without a cluster are
     // not placed), read from the segment ends
     const int64_t placed = ne == 0 ? 0 : (int64_t)__ldcg(p.hcur + (p.K - 1));
-    for (int64_t r0 = warp * kSumRun; r0 < placed; r0 += nwarps * kSumRun) {
-        const int64_t r1 = min(r0 + kSumRun, placed);
+    const int run = (full || ne * 8 > p.N) ? kSumRun : kSumRunMoved;
+    for (int64_t r0 = warp * run; r0 < placed; r0 += nwarps * run) {
+        const int64_t r1 = min(r0 + run, placed);
         float sh[NPER], sl[NPER];
 #pragma unroll
         for (int j = 0; j < NPER; ++j) sh[j] = sl[j] = 0.f;
