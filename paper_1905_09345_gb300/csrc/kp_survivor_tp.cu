@@ -276,6 +276,17 @@ __global__ void __launch_bounds__(kTpThreads, DP > 64 ? 1 : 2) k_survivor_tp(Par
         const unsigned long long c_dist0 = c_dist;  // this lane's count before its point
         if (active) {
             n = p.queue[it];
+            if (Gp * 4 * (DP > 64 ? 256 : 512) <= 128 * 1024) {
+                // the point's stored bound row into L1 now (it is read after the
+                // coordinates, the tightening and the global test): its 128-byte
+                // lines (lb is 128-byte aligned).  Only when the rows of all the
+                // threads an SM holds (512, or 256 at 128 coordinates) fit in
+                // 128 KB of L1; longer rows would evict one another.
+                const uintptr_t r0 = reinterpret_cast<uintptr_t>(p.lb + n * Gp);
+                const uintptr_t r1 = r0 + (uintptr_t)Gp * 4 - 1;
+                for (uintptr_t q = r0 & ~(uintptr_t)127; q <= r1; q += 128)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+            }
             a = p.label[n];
             const uint32_t st = p.stamp[n];
             const int wl = (int)stamp_l(st);
