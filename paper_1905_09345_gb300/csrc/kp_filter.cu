@@ -19,7 +19,7 @@
 //               and the distance calculator over the surviving centroids
 //               (lanes over centroids); refreshes u, lb, lbg and the label,
 //               settles near-ties in FP64, and appends the point to the
-//               moved-point list when its label changes.  Used for D > 64;
+//               moved-point list when its label changes.  Used for D > 128;
 //               smaller D takes the thread-per-point kernel of
 //               kp_survivor_tp.cu.
 #include "kp_common.cuh"

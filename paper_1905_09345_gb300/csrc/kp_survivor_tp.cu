@@ -1,5 +1,5 @@
 // kp_survivor_tp.cu -- the filtered assignment of the survivors, one thread
-// per point (D <= 64).
+// per point (D <= 128).
 //
 // The survivors of the global filter (KPynq Sec. I: the "Multi-level Filters"
 // in front of the "Distance Calculator") mostly need very little work: the
