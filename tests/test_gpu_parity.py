@@ -255,6 +255,22 @@ def test_objective_far_from_origin(kp, offset, algo):
     assert all(s["objective"] < 200.0 * N * D for s in st)  # J is O(N D centre_range^2), not O(N D offset^2)
 
 
+@pytest.mark.parametrize("G", [12, 150])
+def test_survivor_thread_per_point_d128(kp, G):
+    """The thread-per-point survivor kernel at 128 coordinates (the point in
+    registers; K = 600 centroids are too many for shared memory, so their rows
+    are read through L1/L2), filtered path in every iteration after the first:
+    with the bound rows prefetched into L1 (G = 12) and without (G = 150, rows
+    too long for every resident thread's row to fit), labels, centroids and
+    objective in lockstep with the oracle."""
+    rng = np.random.default_rng(31 + G)
+    N, D, K = 8192, 128, 600
+    X, _ = synth.gaussian_mixture(rng, N, D, K, centre_range=6.0, scale="fixed", scale_args=(1.0,))
+    C0 = synth.sample_init(rng, X, K)
+    st = lockstep(kp, X, C0, G, 6, dense_switch=1.0)
+    assert any(s["path"] == kp.KM_PATH_FILTERED for s in st[1:])
+
+
 def test_skewed_reduced_lockstep(kp):
     """The skewed workload's recipe at N=65,536 (power-law sizes, features on
     very different scales far from the origin, integer features, outliers,
