@@ -28,6 +28,9 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 using namespace kp;
 
 static thread_local char g_init_error[512] = "";
+// set while the batched form creates its problems' contexts: those run inside
+// the batch's graph and never launch a fit graph of their own
+static thread_local bool t_ctx_in_batch = false;
 
 namespace kp {
 void set_thread_error(const char *msg) { snprintf(g_init_error, sizeof(g_init_error), "%s", msg); }
@@ -866,6 +869,13 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
             return fail(KM_EINVAL);
         }
     }
+    // the fit graph, recorded now: the host's recording overlaps the device
+    // work enqueued above (with a host X, its copy and split), which the
+    // synchronisation below waits for in any case
+    if (!t_ctx_in_batch && !o.profile) {
+        const int grc = build_fit_graph(c);
+        if (grc != KM_OK) return fail(grc);
+    }
     INIT_CUDA(cudaStreamSynchronize(s));
     *out = c;
     (void)rc;
@@ -1421,7 +1431,9 @@ KM_API int kmeans_batch_init(kmeans_batch **out, int32_t n_problems, const kmean
         o.dense = tv[i].dense;
         o.surv_grab = tv[i].grab;
         kmeans_ctx *c = nullptr;
+        t_ctx_in_batch = true;
         int rc = kmeans_init(&c, static_cast<const float *>(pr.X), pr.N, pr.D, pr.K, pr.G, pr.init_centroids, &o);
+        t_ctx_in_batch = false;
         if (rc) {
             batch_err(b, rc, "problem %d: %s", i, kmeans_last_error(nullptr));
             int keep = rc;
