@@ -182,6 +182,9 @@ KM_API void kmeans_default_options(kmeans_options *opt);
  * init_centroids: K x D float32 (host or device; copied).
  * Requires 1 <= K <= N < 2^31, 1 <= D <= 4096, 1 <= G <= K, K <= 65535.
  * opt may be NULL (defaults).  On success *out receives the context.
+ * Unless profiling, the context's fit graph (kmeans_fit) is recorded here,
+ * while the device still works on the copy of X.  Returns when the device
+ * work it enqueued has finished (a host X is no longer read afterwards).
  * Errors: KM_EINVAL (bad sizes / null pointers / non-finite data when
  * validating), KM_ENOMEM, KM_ECUDA.  On failure *out is NULL and
  * kmeans_last_error(NULL) describes the failure (per thread).
