@@ -4,8 +4,9 @@
 // Two ways, chosen on the device after each assignment, both on the same
 // three kernels: a counting sort of entries by cluster (k_stats_hist counts
 // and lays out the segments, k_stats_scatter places the entries), then each
-// warp sums a run of 64 sorted entries coordinate-parallel and adds one
-// partial per cluster it met to the global FP64 sums.  Global atomics then
+// warp sums a run of sorted entries (64; 16 when few points moved)
+// coordinate-parallel and adds one partial per cluster it met to the global
+// FP64 sums.  Global atomics then
 // touch each cluster a few times instead of once per point.
 //   * full recompute (iteration 0, or more than N/2 labels changed): one
 //     entry per point, under its label; S, Q and the counts start from zero;

@@ -17,18 +17,14 @@
 
 namespace kp {
 
-// two centroids (warps) per block: the FP64 arithmetic of the update (1/64
-// of the FP32 rate on these SMs) is spread over as many SMs as K allows
-constexpr int kUpdWarps = 2;
-constexpr int kUpdGroupsSmem = 2048;  // groups whose drift maxima the last block gathers in shared memory
+constexpr int kUpdWarps = 8;
 
 __device__ __forceinline__ float round_up_f(double x) { return __double2float_ru(x); }
 
 // One warp per centroid; the last block to finish reduces over centroids.
 __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_only, int respect_done) {
-    __shared__ double red_d[kUpdWarps];
-    __shared__ float red_f[kUpdWarps];
-    __shared__ int gmax_s[kUpdGroupsSmem];
+    __shared__ double red_d[kUpdWarps * 32];
+    __shared__ float red_f[kUpdWarps * 32];
     __shared__ int is_last;
     Ctrl *ctrl = p.ctrl;
     count_kernel(ctrl);
@@ -83,47 +79,27 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(Params p, int final_o
     if (!is_last) return;
     __threadfence();
 
-    // objective, in a fixed order (deterministic): strided partial sums, then
-    // the warps' shuffle trees, then the warps in order
+    // objective, in a fixed order (deterministic)
     double jp = 0.0;
-#pragma unroll 4
     for (int kk = threadIdx.x; kk < p.K; kk += blockDim.x) jp += p.Jk[kk];
-    // the largest drift in each group: one centroid per thread into shared
-    // memory (non-negative floats order as their bits), then one group per thread
+    red_d[threadIdx.x] = jp;
     float dmax = 0.f;
     if (!final_only) {
-        const bool in_smem = p.G <= kUpdGroupsSmem;
-        if (in_smem) {
-            for (int g = threadIdx.x; g < p.G; g += blockDim.x) gmax_s[g] = 0;
-            __syncthreads();
-            for (int kk = threadIdx.x; kk < p.K; kk += blockDim.x)
-                atomicMax(&gmax_s[p.grp[kk]], __float_as_int(p.delta[kk]));
-            __syncthreads();
-        }
         for (int g = threadIdx.x; g < p.G; g += blockDim.x) {
             float m = 0.f;
-            if (in_smem) {
-                m = __int_as_float(gmax_s[g]);
-            } else {
-                for (int kk = p.gstart[g]; kk < p.gstart[g + 1]; ++kk) m = fmaxf(m, p.delta[kk]);
-            }
+            for (int kk = p.gstart[g]; kk < p.gstart[g + 1]; ++kk) m = fmaxf(m, p.delta[kk]);
             p.Dg[(size_t)(v + 1) * p.Gp + g] = __fadd_ru(p.Dg[(size_t)v * p.Gp + g], m);
             dmax = fmaxf(dmax, m);
         }
     }
-    jp = warp_sum_d(jp);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    if (lane == 0) {
-        red_d[threadIdx.x >> 5] = jp;
-        red_f[threadIdx.x >> 5] = dmax;
-    }
+    red_f[threadIdx.x] = dmax;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kUpdWarps; ++w) {
-            red_d[0] += red_d[w];
-            red_f[0] = fmaxf(red_f[0], red_f[w]);
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red_d[threadIdx.x] += red_d[threadIdx.x + s];
+            red_f[threadIdx.x] = fmaxf(red_f[threadIdx.x], red_f[threadIdx.x + s]);
         }
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         const double J = red_d[0];
