@@ -202,33 +202,31 @@ __global__ void __launch_bounds__(kSettleThreads, 1) k_settle(Params p, int firs
                 };
                 float s1 = INFINITY, s2 = INFINITY;
                 int bi = q.i1;
-                // one candidate's FP32 distance into the running best and runner-up
-                // (ascending index: a later equal distance does not replace the best)
-                auto take = [&](float d, int col) __attribute__((always_inline)) {
-                    if (d < s1) {
-                        s2 = s1;
-                        s1 = d;
-                        bi = col;
-                    } else {
-                        s2 = fminf(s2, d);
-                    }
-                };
                 for_groups([&](int c0, int c1) __attribute__((always_inline)) {
-                    // four at a time: independent load and reduction chains, so that
-                    // the rows' L2 latency is paid once per four candidates
-                    for (int col = c0; col < c1; col += 4) {
-                        const int nc = min(4, c1 - col);
-                        float pv[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) pv[u] = part(u < nc ? col + u : col);
+                    for (int col = c0; col < c1; col += 2) {  // two at a time: independent chains
+                        const bool two = col + 1 < c1;
+                        float pa = part(col), pb = part(two ? col + 1 : col);
 #pragma unroll
                         for (int o = SUB / 2; o > 0; o >>= 1) {
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) pv[u] += __shfl_xor_sync(smask, pv[u], o, SUB);
+                            pa += __shfl_xor_sync(smask, pa, o, SUB);
+                            pb += __shfl_xor_sync(smask, pb, o, SUB);
                         }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (u < nc) take(pv[u], col + u);
+                        if (pa < s1) {
+                            s2 = s1;
+                            s1 = pa;
+                            bi = col;
+                        } else {
+                            s2 = fminf(s2, pa);
+                        }
+                        if (two) {
+                            if (pb < s1) {
+                                s2 = s1;
+                                s1 = pb;
+                                bi = col + 1;
+                            } else {
+                                s2 = fminf(s2, pb);
+                            }
+                        }
                     }
                 });
                 float bs = s1;
