@@ -308,19 +308,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t n = (int64_t)tile * kTM + r;
             const bool valid = n < p.N;
             int old = -1;
-            float xlo = 0.f, xup = 0.f, E = 0.f;
+            float xlo = 0.f, xup = 0.f, E = 0.f, xn = 0.f;
             bool need_row = false;  // half 0: this row's settle request, written after the conversion
             int best_row = 0;
             float b1_row = 0.f;
             if (half == 0) {
-                // the previous label, read now so that its latency hides behind the scan
+                // the previous label and the row norm, read now so that their
+                // latency hides behind the scan (the error window that needs the
+                // norm is formed after it)
                 old = valid ? (first ? -1 : p.label[n]) : -1;
-                const float xn = valid ? p.xnorm[n] : 0.f;
-                xlo = __fmul_rd(xn, cfg.xn_lo);
-                xup = __fmul_ru(xn, cfg.xn_hi);
-                E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
-                const float R = __fadd_ru(sqrt_hi(xup), cmax);  // bounds ||x - mu|| + ||c - mu||
-                E = __fmaf_ru(p.e_cen, __fmul_ru(R, R), E);
+                xn = valid ? p.xnorm[n] : 0.f;
             }
             const uint32_t tb = tmem + (uint32_t)(grp_id * cfg.buf_cols) + ((uint32_t)(q * 32) << 16);
 
@@ -376,6 +373,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     i1 = bw ? ci : ai;
                     b2 = fminf(fminf(a2, c2), fmaxf(a1, c1));
                 }
+                xlo = __fmul_rd(xn, cfg.xn_lo);
+                xup = __fmul_ru(xn, cfg.xn_hi);
+                E = __fmaf_ru(cfg.e_lin, __fmul_ru(sqrt_hi(xup), cmax), ec2);
+                const float R = __fadd_ru(sqrt_hi(xup), cmax);  // bounds ||x - mu|| + ||c - mu||
+                E = __fmaf_ru(p.e_cen, __fmul_ru(R, R), E);
                 const float twoE = __fmul_ru(2.f, E);
                 const float thr = __fadd_ru(b1, twoE);
 
