@@ -806,19 +806,11 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
         // initial centroids: distances do not change, but the error window of
         // the bfloat16 products scales with ||x - mu|| ||c - mu|| instead of
         // ||x|| ||c||, which matters for data far from the origin
-        std::vector<float> hc((size_t)K * D);
-        INIT_CUDA(cudaMemcpyAsync(hc.data(), init_centroids, hc.size() * 4, cudaMemcpyDefault, s));
-        INIT_CUDA(cudaStreamSynchronize(s));
-        std::vector<float> hm((size_t)p.Dp, 0.f);
-        for (int d = 0; d < D; ++d) {
-            double m = 0.0;
-            for (int k = 0; k < K; ++k) m += hc[(size_t)k * D + d];
-            hm[d] = (float)(m / K);
-        }
+        // (computed on the device from the context's copy of C^0, without a
+        // round trip through the host)
         float *mu;
         INIT_CUDA(dalloc(c, &mu, (size_t)p.Dp));
-        INIT_CUDA(cudaMemcpyAsync(mu, hm.data(), (size_t)p.Dp * 4, cudaMemcpyHostToDevice, s));
-        INIT_CUDA(cudaStreamSynchronize(s));  // hm is a host temporary
+        INIT_CUDA(launch_centroid_mean(p.C, K, D, p.Dp, mu, s));
         p.mu = mu;
         // x - mu and c - mu are each rounded once (relative 2^-24 per coordinate):
         // |s' - s| <= 2 u (1 + u) R^2 + 3 (u (1 + u) R)^2 for R = ||x - mu|| + ||c - mu||

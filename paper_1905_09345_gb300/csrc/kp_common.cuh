@@ -420,5 +420,7 @@ cudaError_t launch_rows_in(const float *in, int D, int K, int Dp, const int32_t 
                            int num_sms);
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t s, int num_sms);
 cudaError_t launch_bf16_to_f32(const uint16_t *in, int64_t n, float *out, cudaStream_t s, int num_sms);
+// mu (Dp floats) = the mean of C's K rows (stride Dp), zero in the padding
+cudaError_t launch_centroid_mean(const float *C, int K, int D, int Dp, float *mu, cudaStream_t s);
 
 }  // namespace kp

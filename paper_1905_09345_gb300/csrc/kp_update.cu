@@ -246,6 +246,25 @@ cudaError_t launch_bounds_out(const Params &p, cudaStream_t s, float *u, float *
     return cudaGetLastError();
 }
 // bfloat16 bit patterns -> FP32 (exact: a bfloat16 is the top half of an FP32)
+// mu[d] = mean over the K rows of C (row stride Dp) of coordinate d, for
+// d < D, summed in FP64 (each thread a strided run of rows in ascending order,
+// then a fixed tree: deterministic) and rounded to FP32; mu[d] = 0 for the
+// padding D <= d < Dp.  One block per coordinate.
+__global__ void __launch_bounds__(256) k_centroid_mean(const float *C, int K, int D, int Dp, float *mu) {
+    __shared__ double part[256];
+    const int d = blockIdx.x;
+    double m = 0.0;
+    if (d < D)
+        for (int k = threadIdx.x; k < K; k += blockDim.x) m += (double)C[(size_t)k * Dp + d];
+    part[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mu[d] = d < D ? (float)(part[0] / (double)K) : 0.f;
+}
+
 __global__ void k_bf16_to_f32(const uint16_t *in, int64_t n, float *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = __uint_as_float((uint32_t)in[i] << 16);
@@ -297,6 +316,11 @@ cudaError_t launch_rows_in(const float *in, int D, int K, int Dp, const int32_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_centroid_mean(const float *C, int K, int D, int Dp, float *mu, cudaStream_t s) {
+    count_launch();
+    k_centroid_mean<<<(unsigned)Dp, 256, 0, s>>>(C, K, D, Dp, mu);
+    return cudaGetLastError();
+}
 cudaError_t launch_bf16_to_f32(const uint16_t *in, int64_t n, float *out, cudaStream_t s, int num_sms) {
     count_launch();
     k_bf16_to_f32<<<num_sms * 8, 256, 0, s>>>(in, n, out);
