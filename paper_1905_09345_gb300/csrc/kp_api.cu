@@ -753,8 +753,8 @@ KM_API int kmeans_init(kmeans_ctx **out, const float *X, int64_t N, int32_t D, i
     if (!cl_orig.empty()) {
         int32_t *orig;
         INIT_CUDA(dalloc(c, &orig, (size_t)K));
+        // (cl_orig, like the group tables below, lives until the final wait)
         INIT_CUDA(cudaMemcpyAsync(orig, cl_orig.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
-        INIT_CUDA(cudaStreamSynchronize(s));  // cl_orig is a host temporary
         p.orig = orig;
     }
     INIT_CUDA(centroids_in(c, init_centroids));
